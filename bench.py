@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Benchmark: spin-images/s and culled point-pairs/s on one GB300, DLS vs STATIC.
+
+Workload: the 100,000-point clustered heightfield (density varying 20:1 over
+[0,1]^2, 32 Gaussian bumps), images for all points, W=32, B=0.01, support
+angle 60 deg.  A step is one pass of the whole path with the inputs already
+resident in HBM: mesh creation (normalise, bounding box), grid build
+(counting sort), and the persistent spin kernel under one loop schedule.  Each
+schedule (STATIC, SS, GSS, FAC) is timed for K steps after W warm-up steps;
+the L2 cache is flushed (a 512 MB write) before every timed step.  `value` is
+the best dynamic schedule.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs the same workload on its own GPU (no
+data exchange: images are independent), timing is max over ranks and value
+is the images of all ranks / that time ("weak" scaling).  ``--impl
+reference`` times the FP64 CPU oracle on a bounded sample of the same
+workload (the only other place this script runs the oracle is the
+cpu_baseline leg).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "spin-images/s & culled point-pairs/s on 1 GB300, DLS vs STATIC; p50/p99 latency"
+UNIT = "spin-images/s"
+SCHEDULES = ("STATIC", "SS", "GSS", "FAC")
+
+
+def _rank_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def _workload():
+    from paper_1811_00901_gb300 import workloads as wl
+    return wl.nonuniform_heightfield()
+
+
+def _config(c, extra=None):
+    d = {"workload": c["name"], "points": int(c["points"].shape[0]), "images": int(c["m"]), "W": int(c["W"]),
+         "bin_size": float(c["bin_size"]), "support_angle_deg": 60.0,
+         "density": "clustered heightfield, 20:1", "l2": "flushed (512 MB write) before each timed step",
+         "inputs": "resident in HBM (device pointers)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# --------------------------------------------------------------------------
+# clocks
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "", 1).isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "", 1).isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if r[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(self.rows), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------
+# roofline helpers
+# --------------------------------------------------------------------------
+
+def _measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("spin_kernel.cu", "device_common.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_1811_00901_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(workload):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "spin_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(workload)
+    if not e or e.get("kernel_source_hash") != _kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# Algorithmic ALU work, per unit (lane-operations; an FMA counts once):
+#   per culled pair (fl32 |X-P|^2 <= Rc2): difference (3), squared norm (3),
+#   compare (1), normal dot (3), compare (1)                        -> 11
+#   per contributing pair: beta (3), n x d (6), its norm (3), sqrt (1),
+#   u, v (2), range tests (3), fixed-point split (6), weights (5),
+#   address (2), four shared-memory int32 atomics (4), count (1)    -> 36
+OPS_PER_CULLED = 11
+OPS_PER_SUPPORT = 36
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    import paper_1811_00901_gb300 as spin
+    from paper_1811_00901_gb300 import _build
+
+    rank, world, local = _rank_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _build.build()
+    c = _workload()
+    n, m, W, B, cs = c["points"].shape[0], c["m"], c["W"], float(c["bin_size"]), float(c["cos_s"])
+    tp = torch.from_numpy(c["points"]).to(dev)
+    tn = torch.from_numpy(c["normals"]).to(dev)
+    out = torch.empty((m, W, W), dtype=torch.int32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def one_step(sched):
+        mesh = spin.si_mesh_create(tp, tn, n, stream)
+        spin.si_generate(mesh, None, m, W, B, cs, sched, out, stream)
+        return mesh
+
+    # ---- counts for the pair metrics (probe run, untimed)
+    sched_probe = spin.make_schedule("GSS")
+    mesh = spin.si_mesh_create(tp, tn, n, stream)
+    culled = torch.zeros(m, dtype=torch.int64, device=dev)
+    support = torch.zeros(m, dtype=torch.int64, device=dev)
+    spin.si_generate_probe(mesh, None, m, W, B, cs, sched_probe, out, culled=culled, support=support,
+                           stream=stream)
+    torch.cuda.synchronize()
+    spin.si_get_stats(mesh)
+    spin.si_mesh_destroy(mesh)
+    n_culled = int(culled.sum().item())
+    n_support = int(support.sum().item())
+
+    results = {}
+    clocks = ClockSampler(local)
+    launches0 = spin.si_kernel_launches()
+    timed_launches = 0
+    kernel_ms = {}
+    clocks.start()
+    for name in SCHEDULES:
+        sched = spin.make_schedule(name)
+        for _ in range(args.warmup):
+            mesh = one_step(sched)
+            stream.synchronize()
+            spin.si_mesh_destroy(mesh)
+        times = []
+        kms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            barrier()
+            spin.si_set_timing(True)
+            l0 = spin.si_kernel_launches()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mesh = one_step(sched)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            timed_launches += spin.si_kernel_launches() - l0
+            spin.si_set_timing(False)
+            st, _ = spin.si_get_stats(mesh)
+            kms.append(st["kernel_ms"] / max(1, st["kernel_launches"]))
+            spin.si_mesh_destroy(mesh)
+            times.append(e0.elapsed_time(e1))
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([sum(times)], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        else:
+            total_ms = sum(times)
+        results[name] = {"ms_per_step": total_ms / args.steps, "images_per_s": world * m * args.steps / (total_ms / 1e3),
+                         "culled_pairs_per_s": world * n_culled * args.steps / (total_ms / 1e3),
+                         "kernel_ms": statistics.median(kms),
+                         "step_ms_p50": statistics.median(times)}
+        kernel_ms[name] = statistics.median(kms)
+    clk = clocks.stop()
+    del launches0
+
+    best = max(("SS", "GSS", "FAC"), key=lambda k: results[k]["images_per_s"])
+    r = results[best]
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if rank == 0 or world > 1:
+        hp = torch.from_numpy(c["points"]).pin_memory()
+        hn = torch.from_numpy(c["normals"]).pin_memory()
+        hout = torch.empty((m, W, W), dtype=torch.int32).pin_memory()
+        sched = spin.make_schedule(best)
+        for _ in range(max(1, args.warmup)):
+            spin.si_generate_host(hp, hn, n, None, m, W, B, cs, sched, hout, stream)
+        et = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            spin.si_generate_host(hp, hn, n, None, m, W, B, cs, sched, hout, stream)
+            et.append(time.perf_counter() - t0)
+        e2e = {"value": m / statistics.median(et), "unit": UNIT, "h2d_bytes_per_step": int(2 * n * 3 * 4),
+               "d2h_bytes_per_step": int(m * W * W * 4), "ms_per_step": 1e3 * statistics.median(et),
+               "api": "si_generate_host (host buffers, copies and mesh/grid build inside)"}
+
+    # ---- roofline of the spin kernel (the dominant kernel)
+    peaks, peak_src = _measured_peaks()
+    f_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    import torch as _t
+    sms = _t.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sms * 128 * f_mhz * 1e6  # lane-ops/s at the maximum SM clock
+    ops = OPS_PER_CULLED * n_culled + OPS_PER_SUPPORT * n_support
+    k_ms = kernel_ms[best]
+    achieved = ops / (k_ms / 1e3)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12, "unit": "Tlane-op/s",
+                "frac": achieved / alu_peak, "traffic": _ncu_traffic(c["name"]),
+                "kernel": "spin_kernel (persistent, %s)" % best, "kernel_ms": k_ms,
+                "peak_source": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)" % (sms, f_mhz, peak_src),
+                "ops_per_culled_pair": OPS_PER_CULLED, "ops_per_support_pair": OPS_PER_SUPPORT,
+                "write_gbs": m * W * W * 4 / (k_ms / 1e3) / 1e9,
+                "write_frac_of_hbm": (m * W * W * 4 / (k_ms / 1e3) / 1e9) / float(peaks.get("hbm_gbs", 6800.0))}
+
+    line = {"metric": METRIC, "value": r["images_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config(c, {"schedule": best, "parallelism": "replicas" if world > 1 else "single GPU"}),
+            "culled_pairs_per_s": r["culled_pairs_per_s"], "culled_pairs_per_step": n_culled,
+            "support_pairs_per_step": n_support,
+            "by_schedule": {k: {"images_per_s": v["images_per_s"], "ms_per_step": v["ms_per_step"],
+                                "kernel_ms": v["kernel_ms"]} for k, v in results.items()},
+            "dls_over_static": r["images_per_s"] / results["STATIC"]["images_per_s"],
+            "e2e": e2e, "roofline": roofline,
+            "gpu_launches": int(timed_launches), "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(c, budget_s=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# CPU legs: the FP64 oracle as it stands
+# --------------------------------------------------------------------------
+
+def _oracle_rate(c, nq, seed=0):
+    import oracle
+    rng = np.random.default_rng(seed)
+    q = np.sort(rng.choice(c["points"].shape[0], nq, replace=False)).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.spin_images(c["points"], c["normals"], c["W"], c["bin_size"], c["cos_s"], query_idx=q)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(c, budget_s=12.0):
+    """Oracle images/s on a random sample sized for ~budget_s seconds."""
+    t = _oracle_rate(c, 8, seed=1)
+    per = t / 8
+    nq = max(8, min(c["m"], int(budget_s / max(per, 1e-6))))
+    t = _oracle_rate(c, nq, seed=2)
+    return {"value": nq / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d random images of the %s workload (all %d points each, FP64, single thread)" % (
+                nq, c["name"], c["points"].shape[0])}
+
+
+def run_reference(args):
+    rank, world, _ = _rank_env()
+    if rank != 0:
+        return
+    c = _workload()
+    per = _oracle_rate(c, 4, seed=3) / 4
+    nq = max(4, int(args.ref_step_seconds / max(per, 1e-6)))
+    for k in range(args.warmup):
+        _oracle_rate(c, max(2, nq // 4), seed=100 + k)
+    times = [_oracle_rate(c, nq, seed=200 + k) for k in range(args.steps)]
+    total = sum(times)
+    value = nq * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(c, {"schedule": "single thread", "sample_images_per_step": nq}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d random images per step of the %s workload" % (nq, c["name"])},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=4.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

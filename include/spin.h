@@ -1,0 +1,254 @@
+/*
+ * spin.h -- C ABI of the GB300 spin-image library (libspin_gb300.so).
+ *
+ * Spin images (Sec. 2.1, Algorithm 1): for every query oriented point P with
+ * unit normal n and every oriented point X of the set (X = P included),
+ *   beta  = n . (X - P),   alpha = |n x (X - P)|  (= sqrt(|X-P|^2 - beta^2)),
+ *   u = W/2 - beta/B (row, from the top),  v = alpha/B (column),
+ * X contributes when n . n_X >= cos S (the support-angle test of Algorithm 1)
+ * and all four bilinear corners lie inside the W x W image:
+ *   0 <= floor(u),  floor(u) + 1 <= W - 1,  floor(v) + 1 <= W - 1.
+ * Each contributing X adds weight 1, split bilinearly over the four corners.
+ *
+ * Output format (every entry point): int32 out[m][W][W], row-major, row i =
+ * u bin, column j = v bin, value = weight x 65536 (16 fractional bits).  The
+ * coordinates are quantised as U = rn(u * 65536), V = rn(v * 65536) (round to
+ * nearest even); with A = U mod 65536, Bq = V mod 65536, i = U >> 16,
+ * j = V >> 16 the corner weights are
+ *   w11 = (A * Bq + 32768) >> 16,  w10 = A - w11,  w01 = Bq - w11,
+ *   w00 = 65536 - A - Bq + w11      (all >= 0, sum exactly 65536),
+ * added at (i,j) w00, (i+1,j) w10, (i,j+1) w01, (i+1,j+1) w11.  Integer
+ * accumulation makes every image independent of scheduling, worker count and
+ * batch composition: results are bit-identical across all of them.
+ *
+ * Image loop scheduling (Sec. 2.2 and Algorithm 3): the loop over images is
+ * run by persistent thread blocks ("workers") that take chunks of the loop
+ * under STATIC, SS, GSS or FAC.  The scheduled iteration is one image GROUP:
+ * `group` consecutive images (in grid order) that a worker generates together
+ * against one shared stream of candidate points.
+ *
+ * Conventions
+ *  - Status codes only; nothing throws across this boundary.
+ *  - Argument errors are reported synchronously; no work is enqueued then.
+ *  - Work is stream-ordered and asynchronous: a call returns after enqueueing.
+ *    The caller synchronises its stream before reading `out`.
+ *  - Device-side conditions (int32 pixel overflow, a bounded wait that gave
+ *    up) are recorded on the mesh and reported by si_get_stats.
+ *  - Pointers named "device" must be CUDA device memory of the current
+ *    device; "host or device" pointers may be either (the library inspects
+ *    them).  The caller owns every buffer it passes; buffers used by an
+ *    enqueued call must stay valid until the stream reaches that point.
+ *  - A NULL stream is the legacy default stream.
+ *  - Handles are not thread-safe, except a server (si_serve_*), whose calls
+ *    may come from any thread.
+ *  - si_last_error() returns a thread-local message about the last failure.
+ */
+#ifndef SPIN_GB300_H
+#define SPIN_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *si_stream; /* the same type as cudaStream_t */
+typedef struct si_mesh_s *si_mesh_t;
+typedef struct si_server_s *si_server_t;
+
+typedef enum si_status {
+    SI_OK = 0,
+    SI_ERR_INVALID = 1,  /* bad argument; nothing was enqueued */
+    SI_ERR_CUDA = 2,     /* a CUDA runtime call failed */
+    SI_ERR_OOM = 3,      /* device or pinned-host allocation failed */
+    SI_ERR_OVERFLOW = 4, /* a pixel exceeded INT32_MAX (more than 32767 points in one pixel) */
+    SI_ERR_TIMEOUT = 5,  /* a wait ran out of time */
+    SI_ERR_BUSY = 6      /* a server refused a request (memory budget / in-flight limit) */
+} si_status;
+
+/* Loop-scheduling rules, Sec. 2.2 (SS, GSS, FAC) and PSIA's static split. */
+typedef enum si_sched_kind {
+    SI_SCHED_STATIC = 0, /* worker k takes groups [floor(kU/P), floor((k+1)U/P)), no atomics */
+    SI_SCHED_SS = 1,     /* one group (min_chunk groups) per request */
+    SI_SCHED_GSS = 2,    /* ceil(remaining / P) groups per request, >= min_chunk */
+    SI_SCHED_FAC = 3     /* batches of P equal chunks of ceil(remaining / (2P)), >= min_chunk */
+} si_sched_kind;
+
+/* Scheduling and launch shape.  Zero fields mean "choose automatically". */
+typedef struct si_schedule {
+    int32_t kind;        /* si_sched_kind */
+    int32_t min_chunk;   /* lower bound of a dynamic chunk, in groups (0 -> 1) */
+    int32_t num_workers; /* persistent thread blocks P (0 -> all SMs x blocks per SM) */
+    int32_t group;       /* images per group: 1, 2, 4, 8, 16 or 32 (0 -> by W) */
+    int32_t grid_div;    /* grid cells per support radius, 1..16 (0 -> 4) */
+} si_schedule;
+
+/* Optional per-image probes (device buffers of m entries, each may be NULL).
+ * Probing slows the kernel down; it is meant for tests and tuning. */
+typedef struct si_probe {
+    int64_t *culled;     /* |{X : fl32(|X-P|^2) <= Rc2}| (candidate set, see si_candidate_rc2) */
+    uint32_t *cand_hash; /* sum over that set of fmix32(index of X), mod 2^32 */
+    int64_t *support;    /* number of contributing X */
+    int32_t *worker;     /* thread block that generated the image */
+    int32_t *step;       /* scheduling step whose chunk contained the image */
+} si_probe;
+
+typedef struct si_stats {
+    int64_t calls;          /* generate calls that used this mesh */
+    int64_t images;         /* images enqueued on this mesh */
+    int32_t overflow;       /* 1 if some pixel of some image exceeded INT32_MAX */
+    int32_t timeout;        /* 1 if a bounded device wait gave up (images incomplete) */
+    int32_t bad_query;      /* 1 if a query index was outside [0, n) (that image is not written) */
+    int32_t reserved;
+    int64_t grid_cells;     /* cells of the most recently built grid */
+    int64_t kernel_launches;/* timed spin-kernel launches (see si_set_timing) */
+    double kernel_ms;       /* their summed device time, CUDA events on the launch stream */
+} si_stats;
+
+/* One item of a batched call: one mesh, its own parameters and output. */
+typedef struct si_batch_item {
+    si_mesh_t mesh;
+    const int32_t *query_idx; /* device [m], or NULL for points 0..m-1 */
+    int64_t m;
+    int32_t W;
+    float bin_size;
+    float cos_support_angle;
+    int32_t *out;             /* device [m][W][W] */
+} si_batch_item;
+
+/* ---------------------------------------------------------------- meshes --
+ * si_mesh_create -- copy an oriented-point set into the library (the input
+ * replication of Sec. 3, "the input data is replicated").
+ *   points, normals : host or device, float[n][3] (x, y, z), n >= 1.
+ *   Normals are normalised in FP32; a zero or non-finite normal or a
+ *   non-finite coordinate is SI_ERR_INVALID.
+ * Synchronises `stream` once (to read back the bounding box).  The mesh is
+ * bound to the current device. */
+si_status si_mesh_create(const float *points, const float *normals, int64_t n,
+                         si_stream stream, si_mesh_t *out_mesh);
+
+/* Waits for the mesh's pending work and frees it. */
+si_status si_mesh_destroy(si_mesh_t mesh);
+
+/* Builds (and caches) the uniform grid that si_generate would use for this
+ * W, bin size and grid_div, so that a later call does no allocation (e.g.
+ * before CUDA-graph capture).  `schedule` may be NULL. */
+si_status si_mesh_prepare(si_mesh_t mesh, int32_t W, float bin_size,
+                          const si_schedule *schedule, si_stream stream);
+
+/* -------------------------------------------------------------- generate --
+ * si_generate -- spin images of m query points (Algorithm 1; the image range
+ * of Algorithm 2 is the chunk a worker receives).
+ *   query_idx : device int32[m] indices into the mesh, or NULL for 0..m-1
+ *               (the paper's "first N oriented points"); m >= 0.
+ *   W         : image width, 2 <= W <= 128.
+ *   bin_size  : B > 0, finite, in the units of the points.
+ *   cos_support_angle : cos S in [-1, 1]; S >= pi is -1 (no angle test).
+ *   out       : device int32[m][W][W].
+ * A query index outside [0, n) is detected on the device: its image is not
+ * written and si_get_stats reports SI_ERR_INVALID (bad_query). */
+si_status si_generate(si_mesh_t mesh, const int32_t *query_idx, int64_t m, int32_t W,
+                      float bin_size, float cos_support_angle, si_schedule schedule,
+                      int32_t *out, si_stream stream);
+
+/* si_generate with per-image probes (see si_probe). */
+si_status si_generate_probe(si_mesh_t mesh, const int32_t *query_idx, int64_t m, int32_t W,
+                            float bin_size, float cos_support_angle, si_schedule schedule,
+                            int32_t *out, const si_probe *probe, si_stream stream);
+
+/* si_generate_batched -- many meshes, each with its own W, B, cos S, queries
+ * and output, in ONE persistent launch: the concatenation of every item's
+ * chunk list is scheduled as one loop (chunks never straddle items).  With
+ * override_or_null == NULL each item's rule comes from the tuning table
+ * (si_tune_*), falling back to GSS.  items: host array of `count` entries. */
+si_status si_generate_batched(const si_batch_item *items, int32_t count,
+                              const si_schedule *override_or_null, si_stream stream);
+
+/* si_generate_host -- the whole path from HOST buffers: copies points and
+ * normals in, builds a temporary mesh, generates, copies the images out to
+ * host memory and synchronises `stream` before returning.
+ *   points, normals : host float[n][3];  query_idx : host int32[m] or NULL;
+ *   out             : host int32[m][W][W] (pinned memory copies fastest). */
+si_status si_generate_host(const float *points, const float *normals, int64_t n,
+                           const int32_t *query_idx, int64_t m, int32_t W, float bin_size,
+                           float cos_support_angle, si_schedule schedule, int32_t *out,
+                           si_stream stream);
+
+/* ------------------------------------------------------------ scheduling --
+ * si_chunk_table -- the chunk boundaries a rule hands out for `units`
+ * iterations and `workers` workers (Algorithm 3's getChunk run to the end):
+ * starts[0] = 0 < starts[1] < ... < starts[nsteps] = units.  For STATIC,
+ * nsteps = workers and empty blocks repeat their start.  `starts` is host
+ * memory of `capacity` entries; if it is too small, *nsteps is still set and
+ * SI_ERR_INVALID is returned. */
+si_status si_chunk_table(int32_t kind, int64_t units, int32_t workers, int32_t min_chunk,
+                         int64_t *starts, int64_t capacity, int64_t *nsteps);
+
+/* The FP32 candidate threshold Rc2 = fl32(R^2 (1 + 1e-5)), R^2 = h^2 +
+ * ((W-1)B)^2, h = W B / 2: every contributing X has |X-P|^2 < R^2, and the
+ * grid examines exactly { X : fl32(|X-P|^2) <= Rc2 } after culling. */
+float si_candidate_rc2(int32_t W, float bin_size);
+
+/* ----------------------------------------------------------------- stats -- */
+/* Synchronises the device and reads the mesh's flags.  Returns
+ * SI_ERR_OVERFLOW, SI_ERR_TIMEOUT or SI_ERR_INVALID (bad query index) when the
+ * corresponding flag is set (the stats are still filled in). */
+si_status si_get_stats(si_mesh_t mesh, si_stats *out);
+/* Clears the mesh's overflow / timeout flags and timing counters. */
+si_status si_reset_stats(si_mesh_t mesh);
+/* When enabled, every spin-kernel launch is bracketed by CUDA events on its
+ * stream and the device time is summed into si_stats of its mesh(es). */
+void si_set_timing(int32_t enabled);
+
+/* --------------------------------------------------------------- tuning --
+ * The autotuner times candidate (rule, min_chunk, workers, group, grid_div)
+ * settings on a mesh and records the fastest per size class (W, log2 of the
+ * point count, log2 of the image count).  si_generate_batched consults it. */
+si_status si_tune_mesh(si_mesh_t mesh, const int32_t *query_idx, int64_t m, int32_t W,
+                       float bin_size, float cos_support_angle, int32_t *scratch_out,
+                       int32_t reps, si_schedule *best, double *best_ms, si_stream stream);
+/* Look up the tuned schedule of a size class; SI_ERR_INVALID if none. */
+si_status si_tune_lookup(int32_t W, int64_t n, int64_t m, si_schedule *out);
+/* Save / load the tuning table as JSON text. */
+si_status si_tune_save(const char *path);
+si_status si_tune_load(const char *path);
+si_status si_tune_clear(void);
+
+/* --------------------------------------------------------------- serving --
+ * A server keeps meshes resident and runs spin-image requests with
+ * continuous batching: requests that arrive while others are on the GPU are
+ * admitted as memory and in-flight slots free up, packed into the next
+ * batched launch, and run on several streams so their work overlaps.
+ *   mem_budget_bytes : device bytes the server may hold for admitted
+ *                      requests (scratch + outputs it allocates)
+ *   max_inflight     : admitted requests at most (>= 1)
+ * si_serve_submit copies req (its device buffers must stay valid until the
+ * request completes).  If req->out is NULL the server allocates the output
+ * from its budget and si_serve_result hands it out.  A request larger than
+ * the whole budget is SI_ERR_BUSY.  Submit never blocks on the GPU. */
+si_status si_serve_create(size_t mem_budget_bytes, int32_t max_inflight, si_server_t *out);
+si_status si_serve_add_mesh(si_server_t s, si_mesh_t mesh, int32_t *mesh_slot);
+si_status si_serve_submit(si_server_t s, const si_batch_item *req, uint64_t *ticket);
+si_status si_serve_poll(si_server_t s, uint64_t ticket, int32_t *done);
+/* Waits for a ticket; SI_ERR_TIMEOUT after timeout_ms (< 0: forever). */
+si_status si_serve_wait(si_server_t s, uint64_t ticket, int32_t timeout_ms);
+/* Device output of a completed ticket (server-allocated when req->out was
+ * NULL) and the submit-to-completion latency in microseconds. */
+si_status si_serve_result(si_server_t s, uint64_t ticket, int32_t **out, double *latency_us);
+/* Releases a completed ticket (and its server-allocated output). */
+si_status si_serve_release(si_server_t s, uint64_t ticket);
+si_status si_serve_destroy(si_server_t s);
+
+/* ----------------------------------------------------------------- misc -- */
+const char *si_last_error(void);
+/* Library version string. */
+const char *si_version(void);
+/* Kernels this library has launched in this process (all devices). */
+int64_t si_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPIN_GB300_H */

@@ -1,0 +1,157 @@
+// internal.h -- shared declarations of the spin-image library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/spin.h"
+
+namespace si {
+
+// ----------------------------------------------------------------- errors --
+void set_error(const char *fmt, ...);
+si_status cuda_fail(cudaError_t e, const char *what);
+
+#define SI_CUDA(call)                                              \
+    do {                                                           \
+        cudaError_t _e = (call);                                   \
+        if (_e != cudaSuccess) return ::si::cuda_fail(_e, #call);  \
+    } while (0)
+
+// ------------------------------------------------------------- constants --
+constexpr int kThreads = 256;       // threads per spin-kernel block (8 warps)
+constexpr int kTile = 256;          // candidate points per staged tile (8 KB)
+constexpr int kStages = 3;          // tile ring depth
+constexpr int kMaxRows = 512;       // stencil rows held in shared memory at once
+constexpr int kMaxW = 128;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // bounded device waits: 2 s
+
+// Device flags (per mesh).
+constexpr unsigned kFlagOverflow = 1u;
+constexpr unsigned kFlagTimeout = 2u;
+constexpr unsigned kFlagBadQuery = 4u;  // a query index outside [0, n): its image is left unwritten
+
+// ------------------------------------------------------------------- grid --
+// A uniform grid over the mesh's bounding box; points counting-sorted by cell.
+struct Grid {
+    float cell = 0.f, inv_cell = 0.f;  // cache key (requested edge), 1 / actual edge
+    float cell_len = 0.f;               // actual edge (>= cell when the grid was coarsened)
+    float origin[3] = {0, 0, 0};
+    int dims[3] = {1, 1, 1};
+    int64_t ncell = 0;
+    int *cell_start = nullptr;  // [ncell + 1]
+    float4 *pn = nullptr;       // [2n]: (x, y, z, orig index bits), (nx, ny, nz, 0)
+    int *sorted_pos = nullptr;  // [n]: original index -> sorted position
+    int *orig_idx = nullptr;    // [n]: sorted position -> original index
+    cudaEvent_t ready = nullptr;
+};
+
+struct Mesh {
+    int device = 0;
+    int64_t n = 0;
+    float4 *pos = nullptr;  // original order, w = 0
+    float4 *nrm = nullptr;  // original order, normalised
+    float bmin[3] = {0, 0, 0}, bmax[3] = {0, 0, 0};
+    std::vector<Grid *> grids;
+    unsigned *flags = nullptr;  // device word: kFlag*
+    cudaEvent_t ready = nullptr;
+    std::mutex mu;
+    int64_t calls = 0, images = 0, last_cells = 0;
+    // timing
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending_events;
+    int64_t timed_launches = 0;
+    double timed_ms = 0.0;
+};
+
+// ---------------------------------------------------------- device items --
+// Everything the persistent kernel needs to know about one item (one mesh
+// with its own parameters).  Lives in device memory.
+struct ItemDesc {
+    const float4 *pn;
+    const int *cell_start;
+    const int *sorted_pos;
+    const int *query_idx;  // [m] or null (0..m-1)
+    const int *perm;       // [m] grid-ordered query t -> query slot q; null: identity order
+    int32_t *out;          // [m][W][W]
+    unsigned *flags;
+    float origin[3];
+    float cell, inv_cell;
+    int dims[3];
+    float margin;          // stencil safety margin (length units)
+    int64_t m;
+    int n_points;          // mesh size (query indices are checked against it)
+    int W;
+    int log2S;             // group = 1 << log2S images
+    float invB, halfW, umax, Rc2, Rc, cosS;
+    int units;             // ceil(m / group)
+    int perm_is_grid;      // perm holds grid orig_idx (all-points query of the mesh)
+    // probes (device, may be null)
+    int64_t *p_culled;
+    uint32_t *p_hash;
+    int64_t *p_support;
+    int32_t *p_worker;
+    int32_t *p_step;
+};
+
+// A piece of the scheduled loop: units [u0, u1) of item `item`.
+struct Piece {
+    int item, u0, u1, pad;
+};
+
+// Launch-wide scratch counters, reset by the last block of each launch.
+struct LaunchCounters {
+    unsigned long long step;         // next dynamic step to hand out
+    unsigned long long done_blocks;  // blocks finished
+};
+
+struct LaunchArgs {
+    const ItemDesc *items;
+    const Piece *pieces;
+    const int *step_piece;  // [nsteps + 1]: pieces of step s are step_piece[s] .. step_piece[s+1]
+    int nsteps;
+    int is_static;          // 1: block b runs step b (no claims)
+    LaunchCounters *ctr;
+    int nitems;
+    int img_words;          // shared words reserved for images (max over items)
+    int probe;
+};
+
+// ---------------------------------------------------------- host helpers --
+Grid *mesh_grid(Mesh *m, float cell, cudaStream_t stream, si_status *st);
+float grid_cell_for(const Mesh *m, int W, float bin, int grid_div);
+int choose_log2_group(int W, int requested_group);
+size_t image_words(int W, int log2S);
+size_t spin_smem_bytes(size_t img_words);
+int blocks_per_sm_for(size_t smem_bytes);
+int num_sms(int device);
+
+// Chunk rules (host side, one implementation for every caller).
+int64_t chunk_table(int kind, int64_t units, int workers, int min_chunk, std::vector<int64_t> *starts);
+
+// Enqueue the generation of a batch of items (host-validated) on `stream`.
+si_status enqueue_batch(const std::vector<si_batch_item> &items, const std::vector<si_schedule> &scheds,
+                        const std::vector<const si_probe *> &probes, cudaStream_t stream,
+                        int forced_workers);
+
+// Pinned staging ring for host->device uploads.
+si_status stage_upload(void *dev_dst, const void *src, size_t bytes, cudaStream_t stream);
+
+// Stream-ordered device allocation (pool-backed).
+si_status dev_alloc(void **p, size_t bytes, cudaStream_t stream);
+void dev_free(void *p, cudaStream_t stream);
+
+// Library kernels launched from host code in other translation units.
+void launch_spin_kernel(const LaunchArgs &a, int blocks, size_t smem, cudaStream_t stream);
+cudaError_t setup_spin_kernel_attributes(size_t smem_bytes);
+
+bool timing_enabled();
+
+// Count of kernels launched by the library (diagnostics).
+void note_launches(int k);
+
+}  // namespace si

@@ -1,0 +1,357 @@
+// mesh.cu -- oriented-point sets resident in HBM and their uniform grids.
+//
+// si_mesh_create replicates the input once on the device (the "input data is
+// replicated" design of Sec. 3): positions and FP32-normalised normals as
+// float4.  Grids are built lazily per cell size and cached on the mesh: a
+// counting sort of the points by cell (cell ids -> histogram -> exclusive
+// scan -> scatter), giving cell_start[] and the points in cell order.
+#include <cmath>
+#include <cstring>
+
+#include "device_common.cuh"
+#include "internal.h"
+#include "scan.h"
+
+namespace si {
+
+namespace {
+
+__global__ void mesh_ingest_kernel(const float *__restrict__ pts, const float *__restrict__ nrm, int64_t n,
+                                   float4 *__restrict__ pos, float4 *__restrict__ nrm_out,
+                                   unsigned *__restrict__ keys /* [6]: min xyz, max xyz */,
+                                   unsigned *__restrict__ bad) {
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    unsigned my_bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
+        float a = nrm[3 * i], b = nrm[3 * i + 1], c = nrm[3 * i + 2];
+        float l2 = a * a + b * b + c * c;
+        bool ok = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(l2) && l2 > 0.0f;
+        if (!ok) {
+            my_bad = 1;
+            l2 = 1.0f;
+        }
+        float inv = 1.0f / sqrtf(l2);
+        pos[i] = make_float4(x, y, z, 0.0f);
+        nrm_out[i] = make_float4(a * inv, b * inv, c * inv, 0.0f);
+        lo[0] = fminf(lo[0], x);
+        lo[1] = fminf(lo[1], y);
+        lo[2] = fminf(lo[2], z);
+        hi[0] = fmaxf(hi[0], x);
+        hi[1] = fmaxf(hi[1], y);
+        hi[2] = fmaxf(hi[2], z);
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], d));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], d));
+        }
+    }
+    my_bad = __any_sync(0xffffffffu, my_bad);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (lo[k] <= hi[k]) {
+                atomicMin(&keys[k], float_key(lo[k]));
+                atomicMax(&keys[3 + k], float_key(hi[k]));
+            }
+        }
+        if (my_bad) atomicOr(bad, 1u);
+    }
+}
+
+struct GridView {
+    float o0, o1, o2, inv;
+    int d0, d1, d2;
+};
+
+__device__ __forceinline__ int cell_of(const GridView &g, float4 p) {
+    int cx = cell_coord(p.x, g.o0, g.inv, g.d0);
+    int cy = cell_coord(p.y, g.o1, g.inv, g.d1);
+    int cz = cell_coord(p.z, g.o2, g.inv, g.d2);
+    return (cz * g.d1 + cy) * g.d0 + cx;
+}
+
+__global__ void grid_count_kernel(const float4 *__restrict__ pos, int64_t n, GridView g, int *__restrict__ hist) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        atomicAdd(&hist[cell_of(g, pos[i])], 1);
+    }
+}
+
+// Scatter into cell order.  Lanes of a warp that share a cell take
+// consecutive slots (warp-aggregated atomics); the order of warps within a
+// cell is whatever the atomics give.  Every result of the library is
+// independent of that order (integer accumulation).
+__global__ void grid_scatter_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm, int64_t n,
+                                    GridView g, int *__restrict__ cursor, float4 *__restrict__ pn,
+                                    int *__restrict__ sorted_pos, int *__restrict__ orig_idx) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) - lane; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = base + lane;
+        bool live = i < n;
+        float4 p = live ? pos[i] : make_float4(0, 0, 0, 0);
+        int c = live ? cell_of(g, p) : -1;
+        unsigned peers = __match_any_sync(0xffffffffu, c);
+        int leader = __ffs(peers) - 1;
+        int rank = __popc(peers & ((1u << lane) - 1u));
+        int slot0 = 0;
+        if (live && lane == leader) slot0 = atomicAdd(&cursor[c], __popc(peers));
+        slot0 = __shfl_sync(0xffffffffu, slot0, leader);
+        if (live) {
+            int s = slot0 + rank;
+            pn[2 * (int64_t)s] = make_float4(p.x, p.y, p.z, __int_as_float((int)i));
+            pn[2 * (int64_t)s + 1] = nrm[i];
+            sorted_pos[i] = s;
+            orig_idx[s] = (int)i;
+        }
+    }
+}
+
+int grid_blocks(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+void free_grid(Grid *g) {
+    if (!g) return;
+    cudaFree(g->cell_start);
+    cudaFree(g->pn);
+    cudaFree(g->sorted_pos);
+    cudaFree(g->orig_idx);
+    if (g->ready) cudaEventDestroy(g->ready);
+    delete g;
+}
+
+bool is_device_pointer(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+// Cell edge for a call: the candidate radius divided by grid_div, rounded down
+// to a quarter octave so that calls with nearby (W, B) share one grid.
+float grid_cell_for(const Mesh *m, int W, float bin, int grid_div) {
+    (void)m;
+    double R = std::sqrt((double)si_candidate_rc2(W, bin));
+    int div = grid_div > 0 ? grid_div : 4;
+    double c = R / div;
+    double e = std::floor(std::log2(c) * 4.0) / 4.0;
+    return (float)std::exp2(e);
+}
+
+Grid *mesh_grid(Mesh *m, float cell, cudaStream_t stream, si_status *st) {
+    *st = SI_OK;
+    std::lock_guard<std::mutex> lk(m->mu);
+    for (Grid *g : m->grids)
+        if (g->cell == cell) {
+            cudaError_t e = cudaStreamWaitEvent(stream, g->ready, 0);
+            if (e != cudaSuccess) {
+                *st = cuda_fail(e, "cudaStreamWaitEvent(grid)");
+                return nullptr;
+            }
+            return g;
+        }
+    // build a new grid
+    double ext[3], cellv = cell;
+    int64_t ncell = 0;
+    int dims[3];
+    for (int guard = 0; guard < 64; ++guard) {
+        ncell = 1;
+        for (int k = 0; k < 3; ++k) {
+            ext[k] = (double)m->bmax[k] - (double)m->bmin[k];
+            double d = std::ceil(ext[k] / cellv);
+            if (d < 1) d = 1;
+            if (d > (1 << 20)) d = 1 << 20;
+            dims[k] = (int)d;
+            ncell *= dims[k];
+        }
+        if (ncell <= (int64_t(1) << 24) && ncell <= 64 * m->n + 4096) break;
+        cellv *= 1.25;
+    }
+    Grid *g = new Grid();
+    g->cell = cell;  // cache key stays the requested cell
+    g->inv_cell = (float)(1.0 / cellv);
+    g->cell_len = (float)cellv;
+    for (int k = 0; k < 3; ++k) {
+        g->origin[k] = m->bmin[k];
+        g->dims[k] = dims[k];
+    }
+    g->ncell = ncell;
+    cudaError_t e;
+    e = cudaMalloc(&g->cell_start, sizeof(int) * (ncell + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->pn, sizeof(float4) * 2 * m->n);
+    if (e == cudaSuccess) e = cudaMalloc(&g->sorted_pos, sizeof(int) * m->n);
+    if (e == cudaSuccess) e = cudaMalloc(&g->orig_idx, sizeof(int) * m->n);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ready, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        *st = cuda_fail(e, "grid allocation");
+        free_grid(g);
+        return nullptr;
+    }
+    GridView gv{g->origin[0], g->origin[1], g->origin[2], g->inv_cell, dims[0], dims[1], dims[2]};
+    int *cursor = nullptr;
+    do {
+        e = cudaStreamWaitEvent(stream, m->ready, 0);
+        if (e != cudaSuccess) break;
+        e = cudaMemsetAsync(g->cell_start, 0, sizeof(int) * (ncell + 1), stream);
+        if (e != cudaSuccess) break;
+        grid_count_kernel<<<grid_blocks(m->n), 256, 0, stream>>>(m->pos, m->n, gv, g->cell_start);
+        note_launches(1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) break;
+        *st = scan_exclusive(g->cell_start, g->cell_start, ncell + 1, stream);
+        if (*st != SI_OK) break;
+        *st = dev_alloc((void **)&cursor, sizeof(int) * ncell, stream);
+        if (*st != SI_OK) break;
+        e = cudaMemcpyAsync(cursor, g->cell_start, sizeof(int) * ncell, cudaMemcpyDeviceToDevice, stream);
+        if (e != cudaSuccess) break;
+        grid_scatter_kernel<<<grid_blocks(m->n), 256, 0, stream>>>(m->pos, m->nrm, m->n, gv, cursor, g->pn,
+                                                                  g->sorted_pos, g->orig_idx);
+        note_launches(1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) break;
+        e = cudaEventRecord(g->ready, stream);
+    } while (0);
+    if (cursor) dev_free(cursor, stream);
+    if (e != cudaSuccess && *st == SI_OK) *st = cuda_fail(e, "grid build");
+    if (*st != SI_OK) {
+        cudaStreamSynchronize(stream);
+        free_grid(g);
+        return nullptr;
+    }
+    m->grids.push_back(g);
+    m->last_cells = ncell;
+    return g;
+}
+
+}  // namespace si
+
+using namespace si;
+
+extern "C" {
+
+si_status si_mesh_create(const float *points, const float *normals, int64_t n, si_stream stream,
+                         si_mesh_t *out_mesh) {
+    if (!out_mesh) {
+        set_error("si_mesh_create: out_mesh is NULL");
+        return SI_ERR_INVALID;
+    }
+    *out_mesh = nullptr;
+    if (!points || !normals || n < 1 || n > (int64_t(1) << 30)) {
+        set_error("si_mesh_create: need non-NULL points/normals and 1 <= n <= 2^30 (n = %lld)", (long long)n);
+        return SI_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Mesh *m = new Mesh();
+    SI_CUDA(cudaGetDevice(&m->device));
+    m->n = n;
+    const float *dp = points, *dn = normals;
+    float *tmp_p = nullptr, *tmp_n = nullptr;
+    unsigned *scratch = nullptr;  // 6 bbox keys + 1 bad flag
+    unsigned host_scratch[7];
+    si_status st = SI_OK;
+    cudaError_t e = cudaSuccess;
+    do {
+        e = cudaMalloc(&m->pos, sizeof(float4) * n);
+        if (e == cudaSuccess) e = cudaMalloc(&m->nrm, sizeof(float4) * n);
+        if (e == cudaSuccess) e = cudaMalloc(&m->flags, sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->ready, cudaEventDisableTiming);
+        if (e != cudaSuccess) break;
+        e = cudaMemsetAsync(m->flags, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) break;
+        if (!is_device_pointer(points)) {
+            if ((st = dev_alloc((void **)&tmp_p, sizeof(float) * 3 * n, s)) != SI_OK) break;
+            e = cudaMemcpyAsync(tmp_p, points, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) break;
+            dp = tmp_p;
+        }
+        if (!is_device_pointer(normals)) {
+            if ((st = dev_alloc((void **)&tmp_n, sizeof(float) * 3 * n, s)) != SI_OK) break;
+            e = cudaMemcpyAsync(tmp_n, normals, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) break;
+            dn = tmp_n;
+        }
+        if ((st = dev_alloc((void **)&scratch, sizeof(unsigned) * 8, s)) != SI_OK) break;
+        unsigned init[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 0u, 0u};
+        e = cudaMemcpyAsync(scratch, init, sizeof(init), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) break;
+        mesh_ingest_kernel<<<grid_blocks(n), 256, 0, s>>>(dp, dn, n, m->pos, m->nrm, scratch, scratch + 6);
+        note_launches(1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) break;
+        e = cudaMemcpyAsync(host_scratch, scratch, sizeof(host_scratch), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) break;
+        e = cudaEventRecord(m->ready, s);
+        if (e != cudaSuccess) break;
+        e = cudaStreamSynchronize(s);
+    } while (0);
+    if (tmp_p) dev_free(tmp_p, s);
+    if (tmp_n) dev_free(tmp_n, s);
+    if (scratch) dev_free(scratch, s);
+    if (e != cudaSuccess && st == SI_OK) st = cuda_fail(e, "si_mesh_create");
+    if (st == SI_OK && host_scratch[6] != 0) {
+        set_error("si_mesh_create: a coordinate is not finite or a normal has zero length");
+        st = SI_ERR_INVALID;
+    }
+    if (st != SI_OK) {
+        cudaStreamSynchronize(s);
+        cudaFree(m->pos);
+        cudaFree(m->nrm);
+        cudaFree(m->flags);
+        if (m->ready) cudaEventDestroy(m->ready);
+        delete m;
+        return st;
+    }
+    for (int k = 0; k < 3; ++k) {
+        unsigned klo = host_scratch[k], khi = host_scratch[3 + k];
+        unsigned blo = (klo & 0x80000000u) ? (klo & 0x7fffffffu) : ~klo;
+        unsigned bhi = (khi & 0x80000000u) ? (khi & 0x7fffffffu) : ~khi;
+        std::memcpy(&m->bmin[k], &blo, 4);
+        std::memcpy(&m->bmax[k], &bhi, 4);
+    }
+    *out_mesh = reinterpret_cast<si_mesh_t>(m);
+    return SI_OK;
+}
+
+si_status si_mesh_destroy(si_mesh_t mesh) {
+    if (!mesh) {
+        set_error("si_mesh_destroy: NULL mesh");
+        return SI_ERR_INVALID;
+    }
+    Mesh *m = reinterpret_cast<Mesh *>(mesh);
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(m->device);
+    cudaDeviceSynchronize();
+    for (Grid *g : m->grids) free_grid(g);
+    for (auto &pe : m->pending_events) {
+        cudaEventDestroy(pe.first);
+        cudaEventDestroy(pe.second);
+    }
+    cudaFree(m->pos);
+    cudaFree(m->nrm);
+    cudaFree(m->flags);
+    if (m->ready) cudaEventDestroy(m->ready);
+    delete m;
+    cudaSetDevice(prev);
+    return SI_OK;
+}
+
+float si_candidate_rc2(int32_t W, float bin_size) {
+    double B = (double)bin_size;
+    double h = (double)W * B / 2.0;
+    double r = (double)(W - 1) * B;
+    return (float)((h * h + r * r) * (1.0 + 1e-5));
+}
+
+}  // extern "C"

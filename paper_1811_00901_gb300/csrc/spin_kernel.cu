@@ -1,0 +1,487 @@
+// spin_kernel.cu -- the persistent spin-image kernel (Algorithm 1's image loop
+// as run by the workers of Algorithms 2-4, one GPU edition).
+//
+// Work decomposition
+//   * The scheduled loop runs over image GROUPS: `S` consecutive query points
+//     in grid (cell) order, generated together by one thread block against a
+//     shared stream of candidate points.
+//   * A block is a worker.  Under STATIC, block b runs step b (its block of
+//     the loop, PSIA).  Under SS / GSS / FAC one thread claims the next step
+//     with a global atomicAdd (the master's getChunk of Algorithm 3 is the
+//     precomputed step table; the request/assign exchange is the atomic) and
+//     broadcasts it through shared memory.
+//   * For a group, the candidate points are the grid cells within the
+//     candidate radius Rc of the group's bounding box, enumerated as
+//     (z, y) rows of contiguous cells.  One thread streams them into a ring
+//     of shared-memory tiles with 1-D bulk copies (TMA, mbarrier completion);
+//     all threads consume the tiles.
+//   * Lane l of a warp works on image slot (l mod S) against candidate
+//     (l div S) of the warp's current step, so one candidate read is broadcast
+//     to S lanes and the S images of a group are interleaved word by word in
+//     shared memory (pixel p of slot q at word p*S + q): the 32 lanes of a
+//     warp hit at most 32/S words per bank, whatever pixels they splat.
+//
+// Per pair (P = query, X = candidate, FP32, differences taken directly):
+//   d = X - P; cull if fl32(|d|^2) > Rc2; angle test n.n_X >= cos S;
+//   beta = n.d; alpha = |n x d|; u = W/2 - beta/B; v = alpha/B;
+//   support test 0 <= u < W-1, v < W-1; fixed-point bilinear splat of weight
+//   65536 with four shared-memory int32 atomics.
+// Images hold (W+1) x (W+1) words per slot: the extra row and column absorb
+// the zero-weight corners of points whose coordinate rounds up onto W-1.
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace si {
+
+namespace {
+
+constexpr int kWarps = kThreads / 32;
+
+struct __align__(16) QueryInfo {
+    float4 p;
+    float4 n;
+    int slot;
+    int pad[3];
+};
+
+struct __align__(16) Header {
+    uint64_t bar[kStages];
+    int claim;
+    int total;
+    float gmin[3], gmax[3];
+    int ylo, yhi, zlo, zhi;
+    int warp_tmp[kWarps];
+    unsigned long long grp_weight;
+    unsigned long long grp_pix;
+};
+
+constexpr int kHeaderBytes = 256;
+static_assert(sizeof(Header) <= kHeaderBytes, "header too large");
+constexpr int kQueryBytes = 32 * sizeof(QueryInfo);
+constexpr int kRowBytes = 3 * (kMaxRows + 4) * sizeof(int);
+constexpr int kProbeBytes = 3 * 32 * sizeof(int);
+constexpr int kTileBytes = kStages * kTile * 32;
+
+constexpr int off_query() { return kHeaderBytes; }
+constexpr int off_rows() { return off_query() + kQueryBytes; }
+constexpr int off_probe() { return off_rows() + kRowBytes; }
+constexpr int off_tiles() { return (off_probe() + kProbeBytes + 127) & ~127; }
+constexpr int off_images() { return off_tiles() + kTileBytes; }
+
+// Exclusive scan of len[0..nr) into off[0..nr); returns the total to all threads.
+__device__ int block_scan_rows(const int *len, int *off, int nr, Header &H) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int i0 = 2 * tid, i1 = 2 * tid + 1;
+    const int a0 = i0 < nr ? len[i0] : 0;
+    const int a1 = i1 < nr ? len[i1] : 0;
+    const int s = a0 + a1;
+    int incl = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int o = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += o;
+    }
+    if (lane == 31) H.warp_tmp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int v = lane < kWarps ? H.warp_tmp[lane] : 0;
+        int vi = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int o = __shfl_up_sync(0xffffffffu, vi, d);
+            if (lane >= d) vi += o;
+        }
+        if (lane < kWarps) H.warp_tmp[lane] = vi - v;
+        if (lane == kWarps - 1) H.total = vi;
+    }
+    __syncthreads();
+    const int excl = H.warp_tmp[warp] + incl - s;
+    if (i0 < nr) off[i0] = excl;
+    if (i1 < nr) off[i1] = excl + a0;
+    const int total = H.total;
+    __syncthreads();
+    return total;
+}
+
+template <bool PROBE>
+__device__ __forceinline__ void splat_pair(const float4 X, const float4 NX, const float4 P, const float4 N,
+                                           const float Rc2, const float cosS, const float invB,
+                                           const float halfW, const float umax, int *img_q, const int row_words,
+                                           const int S, const int log2S, int &cnt, int *pc_c, int *pc_s,
+                                           unsigned *pc_h) {
+    // The candidate-set expression: exactly fl32(fma(dz,dz, fma(dy,dy, dx*dx))).
+    const float dx = __fsub_rn(X.x, P.x);
+    const float dy = __fsub_rn(X.y, P.y);
+    const float dz = __fsub_rn(X.z, P.z);
+    const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    if (PROBE && d2 <= Rc2) {
+        atomicAdd(pc_c, 1);
+        atomicAdd(pc_h, fmix32(__float_as_uint(X.w)));
+    }
+    const float ca = fmaf(N.z, NX.z, fmaf(N.y, NX.y, N.x * NX.x));
+    if (!(d2 <= Rc2) || !(ca >= cosS)) return;
+    const float beta = fmaf(N.z, dz, fmaf(N.y, dy, N.x * dx));
+    const float cx = fmaf(N.y, dz, -N.z * dy);
+    const float cy = fmaf(N.z, dx, -N.x * dz);
+    const float cz = fmaf(N.x, dy, -N.y * dx);
+    const float a2 = fmaf(cz, cz, fmaf(cy, cy, cx * cx));
+    const float u = __fmaf_rn(-beta, invB, halfW);
+    const float v = sqrtf(a2) * invB;
+    if (!(u >= 0.0f) || !(u < umax) || !(v < umax)) return;
+    if (PROBE) atomicAdd(pc_s, 1);
+    ++cnt;
+    // U = rn(u * 2^16): u * 2^16 is exact, adding 2^23 rounds it to an integer
+    // in the low mantissa bits (0 <= U < 2^23 because u < W - 1 <= 127).
+    const int U = __float_as_int(__fmaf_rn(u, 65536.0f, 8388608.0f)) - 0x4B000000;
+    const int V = __float_as_int(__fmaf_rn(v, 65536.0f, 8388608.0f)) - 0x4B000000;
+    const unsigned A = (unsigned)U & 0xFFFFu;
+    const unsigned Bq = (unsigned)V & 0xFFFFu;
+    const int i = U >> 16, j = V >> 16;
+    const unsigned w11 = (A * Bq + 32768u) >> 16;
+    const int w10 = (int)(A - w11);
+    const int w01 = (int)(Bq - w11);
+    const int w00 = (int)(65536u - A - Bq + w11);
+    int *p0 = img_q + ((i * row_words + j * S));
+    atomicAdd(p0, w00);
+    atomicAdd(p0 + row_words, w10);
+    atomicAdd(p0 + S, w01);
+    atomicAdd(p0 + row_words + S, (int)w11);
+    (void)log2S;
+}
+
+template <bool PROBE>
+__global__ void __launch_bounds__(kThreads) spin_kernel(LaunchArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    Header &H = *reinterpret_cast<Header *>(smem);
+    QueryInfo *Q = reinterpret_cast<QueryInfo *>(smem + off_query());
+    int *row_start = reinterpret_cast<int *>(smem + off_rows());
+    int *row_len = row_start + (kMaxRows + 4);
+    int *row_off = row_len + (kMaxRows + 4);
+    int *pc_culled = reinterpret_cast<int *>(smem + off_probe());
+    int *pc_support = pc_culled + 32;
+    unsigned *pc_hash = reinterpret_cast<unsigned *>(pc_support + 32);
+    float4 *tiles = reinterpret_cast<float4 *>(smem + off_tiles());
+    int *img = reinterpret_cast<int *>(smem + off_images());
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    if (tid == 0) {
+        for (int b = 0; b < kStages; ++b) mbar_init(&H.bar[b], 1);
+        fence_mbar_init();
+        H.grp_weight = 0;
+        H.grp_pix = 0;
+    }
+    __syncthreads();
+
+    uint32_t phase_bits = 0;  // expected parity per stage (every thread tracks it)
+    uint32_t armed = 0;       // stages with a fill in flight (thread 0)
+    bool aborted = false;
+    int claim_iter = 0;
+
+    while (!aborted) {
+        __syncthreads();
+        if (tid == 0) {
+            int s;
+            if (a.is_static)
+                s = claim_iter == 0 ? (int)blockIdx.x : a.nsteps;
+            else
+                s = (int)atomicAdd(&a.ctr->step, 1ull);
+            H.claim = s;
+        }
+        __syncthreads();
+        const int step = H.claim;
+        ++claim_iter;
+        if (step >= a.nsteps) break;
+
+        for (int pi = a.step_piece[step]; pi < a.step_piece[step + 1] && !aborted; ++pi) {
+            const Piece pc = a.pieces[pi];
+            const ItemDesc &it = a.items[pc.item];
+            const int log2S = it.log2S, S = 1 << log2S;
+            const int W = it.W, W1 = W + 1;
+            const int row_words = W1 << log2S;
+            const int64_t m = it.m;
+            const float4 *__restrict__ pn = it.pn;
+            const int *__restrict__ cstart = it.cell_start;
+            const float ox = it.origin[0], oy = it.origin[1], oz = it.origin[2];
+            const float cell = it.cell, inv = it.inv_cell, margin = it.margin;
+            const int dx_ = it.dims[0], dy_ = it.dims[1], dz_ = it.dims[2];
+            const float Rc2 = it.Rc2, Rc = it.Rc, cosS = it.cosS, invB = it.invB, halfW = it.halfW,
+                        umax = it.umax;
+            const int slot = lane & (S - 1);
+            const int sub = lane >> log2S;
+            const int cpw = 32 >> log2S;
+            const int img_words_pad = ((S * W1 * W1) + 3) & ~3;
+
+            for (int u = pc.u0; u < pc.u1 && !aborted; ++u) {
+                const int64_t t0 = (int64_t)u << log2S;
+                const int nq = (int)(m - t0 < (int64_t)S ? m - t0 : (int64_t)S);
+                // ---- queries of the group
+                if (tid < S) {
+                    if (tid < nq) {
+                        const int64_t t = t0 + tid;
+                        const int q = it.perm ? it.perm[t] : (int)t;
+                        int sp = (int)t;
+                        bool ok = true;
+                        if (!it.perm_is_grid) {
+                            const int src = it.query_idx ? it.query_idx[q] : q;
+                            ok = (unsigned)src < (unsigned)it.n_points;
+                            sp = ok ? it.sorted_pos[src] : 0;
+                        }
+                        if (!ok) atomicOr(it.flags, kFlagBadQuery);
+                        Q[tid].p = pn[2 * (int64_t)sp];
+                        Q[tid].n = pn[2 * (int64_t)sp + 1];
+                        Q[tid].slot = ok ? q : -1;
+                    } else {
+                        Q[tid].slot = -1;
+                    }
+                }
+                if (PROBE && tid < 32) {
+                    pc_culled[tid] = 0;
+                    pc_support[tid] = 0;
+                    pc_hash[tid] = 0;
+                }
+                {
+                    int4 *z4 = reinterpret_cast<int4 *>(img);
+                    for (int k = tid; k < img_words_pad / 4; k += kThreads) z4[k] = make_int4(0, 0, 0, 0);
+                }
+                __syncthreads();
+                // ---- bounding box of the group and the stencil's y/z cell range
+                if (warp == 0) {
+                    float lo0 = INFINITY, lo1 = INFINITY, lo2 = INFINITY;
+                    float hi0 = -INFINITY, hi1 = -INFINITY, hi2 = -INFINITY;
+                    if (lane < nq) {
+                        const float4 p = Q[lane].p;
+                        lo0 = hi0 = p.x;
+                        lo1 = hi1 = p.y;
+                        lo2 = hi2 = p.z;
+                    }
+#pragma unroll
+                    for (int d = 16; d > 0; d >>= 1) {
+                        lo0 = fminf(lo0, __shfl_xor_sync(0xffffffffu, lo0, d));
+                        lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, d));
+                        lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, d));
+                        hi0 = fmaxf(hi0, __shfl_xor_sync(0xffffffffu, hi0, d));
+                        hi1 = fmaxf(hi1, __shfl_xor_sync(0xffffffffu, hi1, d));
+                        hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, d));
+                    }
+                    if (lane == 0) {
+                        H.gmin[0] = lo0;
+                        H.gmin[1] = lo1;
+                        H.gmin[2] = lo2;
+                        H.gmax[0] = hi0;
+                        H.gmax[1] = hi1;
+                        H.gmax[2] = hi2;
+                        const float r = Rc + margin;
+                        H.ylo = cell_coord(lo1 - r, oy, inv, dy_);
+                        H.yhi = cell_coord(hi1 + r, oy, inv, dy_);
+                        H.zlo = cell_coord(lo2 - r, oz, inv, dz_);
+                        H.zhi = cell_coord(hi2 + r, oz, inv, dz_);
+                    }
+                }
+                __syncthreads();
+                // query point and normal of this lane's slot
+                const float4 qP = Q[slot].p;
+                const float4 qN = Q[slot].n;
+                const bool active = slot < nq;
+                int cnt = 0;
+                int *img_q = img + slot;
+                const float gmin0 = H.gmin[0], gmin1 = H.gmin[1], gmin2 = H.gmin[2];
+                const float gmax0 = H.gmax[0], gmax1 = H.gmax[1], gmax2 = H.gmax[2];
+                const int ylo = H.ylo, zlo = H.zlo;
+                const int ny = H.yhi - ylo + 1, nz = H.zhi - zlo + 1;
+                const int nrows_total = ny * nz;
+
+                for (int rb = 0; rb < nrows_total && !aborted; rb += kMaxRows) {
+                    const int nr = min(kMaxRows, nrows_total - rb);
+                    // ---- candidate rows: for each (z, y) the x range of cells within Rc
+                    for (int r = tid; r < nr; r += kThreads) {
+                        const int rr = rb + r;
+                        const int y = ylo + rr % ny, z = zlo + rr / ny;
+                        const float sy0 = fmaf((float)y, cell, oy), sy1 = sy0 + cell;
+                        const float sz0 = fmaf((float)z, cell, oz), sz1 = sz0 + cell;
+                        const float gy = fmaxf(0.0f, fmaxf(sy0 - gmax1, gmin1 - sy1) - margin);
+                        const float gz = fmaxf(0.0f, fmaxf(sz0 - gmax2, gmin2 - sz1) - margin);
+                        const float rem = Rc2 - gy * gy - gz * gz;
+                        int start = 0, len = 0;
+                        if (rem >= 0.0f) {
+                            const float rx = sqrtf(rem) + margin;
+                            const int x0 = cell_coord(gmin0 - rx, ox, inv, dx_);
+                            const int x1 = cell_coord(gmax0 + rx, ox, inv, dx_);
+                            const int c0 = (z * dy_ + y) * dx_ + x0;
+                            start = cstart[c0];
+                            len = cstart[c0 + (x1 - x0) + 1] - start;
+                        }
+                        row_start[r] = start;
+                        row_len[r] = len;
+                    }
+                    __syncthreads();
+                    const int total = block_scan_rows(row_len, row_off, nr, H);
+                    const int ntiles = (total + kTile - 1) / kTile;
+                    // ---- producer state (thread 0): row cursor
+                    int cr = 0, co = 0;
+                    auto fill = [&](int k) {
+                        const int b = k % kStages;
+                        const int need = min(kTile, total - k * kTile);
+                        float4 *dst = tiles + (size_t)b * kTile * 2;
+                        fence_proxy_async_smem();
+                        mbar_arrive_expect_tx(&H.bar[b], (uint32_t)need * 32u);
+                        int done = 0;
+                        while (done < need && cr < nr) {
+                            const int avail = row_len[cr] - co;
+                            if (avail <= 0) {
+                                ++cr;
+                                co = 0;
+                                continue;
+                            }
+                            const int take = min(need - done, avail);
+                            bulk_copy_g2s(dst + 2 * done, pn + 2 * (int64_t)(row_start[cr] + co),
+                                          (uint32_t)take * 32u, &H.bar[b]);
+                            done += take;
+                            co += take;
+                        }
+                        armed |= 1u << b;
+                    };
+                    if (tid == 0) {
+                        for (int k = 0; k < kStages && k < ntiles; ++k) fill(k);
+                    }
+                    for (int k = 0; k < ntiles; ++k) {
+                        const int b = k % kStages;
+                        const bool ok = mbar_wait_bounded(&H.bar[b], (phase_bits >> b) & 1u, kWaitLimitNs);
+                        if (ok) {
+                            phase_bits ^= 1u << b;
+                            if (tid == 0) armed &= ~(1u << b);
+                            const int len = min(kTile, total - k * kTile);
+                            const float4 *tile = tiles + (size_t)b * kTile * 2;
+                            if (active) {
+#pragma unroll 2
+                                for (int c = warp * cpw + sub; c < len; c += kWarps * cpw) {
+                                    const float4 X = tile[2 * c];
+                                    const float4 NX = tile[2 * c + 1];
+                                    splat_pair<PROBE>(X, NX, qP, qN, Rc2, cosS, invB, halfW, umax, img_q,
+                                                      row_words, S, log2S, cnt, pc_culled + slot,
+                                                      pc_support + slot, pc_hash + slot);
+                                }
+                            }
+                        }
+                        if (__syncthreads_or(!ok)) {
+                            aborted = true;
+                            break;
+                        }
+                        if (tid == 0 && k + kStages < ntiles) fill(k + kStages);
+                    }
+                }
+                if (aborted) {
+                    if (tid == 0) {
+                        atomicOr(it.flags, kFlagTimeout);
+                        // drain this block's copies still in flight before leaving
+                        for (int b = 0; b < kStages; ++b)
+                            if (armed & (1u << b)) mbar_wait_bounded(&H.bar[b], (phase_bits >> b) & 1u, kWaitLimitNs);
+                    }
+                    break;
+                }
+                __syncthreads();
+                // ---- write-out: pixel (i, j) of slot q lives at ((i*(W+1) + j) * S + q)
+                long long pix = 0;
+                const int npix = W * W;
+                int32_t *__restrict__ out = it.out;
+                for (int k = tid; k < (npix << log2S); k += kThreads) {
+                    const int q = k & (S - 1);
+                    if (q >= nq) continue;
+                    const int p = k >> log2S;
+                    const int i = p / W, j = p - i * W;
+                    const int v = img[(i * W1 + j) * S + q];
+                    const int qs = Q[q].slot;
+                    if (qs >= 0) __stcs(out + (int64_t)qs * npix + p, v);
+                    pix += v;
+                }
+                // ---- exact overflow check of the group: the written pixels
+                // (int32 read as signed) sum to 65536 x pairs unless a pixel wrapped
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) {
+                    pix += __shfl_xor_sync(0xffffffffu, pix, d);
+                    cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+                }
+                if (lane == 0) {
+                    atomicAdd(&H.grp_pix, (unsigned long long)pix);
+                    atomicAdd(&H.grp_weight, (unsigned long long)cnt * 65536ull);
+                }
+                if (PROBE && tid < nq && Q[tid].slot >= 0) {
+                    const int q = Q[tid].slot;
+                    if (it.p_culled) it.p_culled[q] = pc_culled[tid];
+                    if (it.p_hash) it.p_hash[q] = pc_hash[tid];
+                    if (it.p_support) it.p_support[q] = pc_support[tid];
+                    if (it.p_worker) it.p_worker[q] = (int)blockIdx.x;
+                    if (it.p_step) it.p_step[q] = step;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    if (H.grp_pix != H.grp_weight) atomicOr(it.flags, kFlagOverflow);
+                    H.grp_pix = 0;
+                    H.grp_weight = 0;
+                }
+            }
+        }
+    }
+    // ---- the last block to finish resets the dynamic step counter for the next launch
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const unsigned long long prev = atomicAdd(&a.ctr->done_blocks, 1ull);
+        if (prev == gridDim.x - 1) {
+            atomicExch(&a.ctr->step, 0ull);
+            atomicExch(&a.ctr->done_blocks, 0ull);
+        }
+    }
+}
+
+}  // namespace
+
+size_t image_words(int W, int log2S) {
+    size_t w = (size_t)(W + 1) * (W + 1) << log2S;
+    return (w + 3) & ~size_t(3);
+}
+
+size_t spin_smem_bytes(size_t img_words) { return (size_t)off_images() + img_words * sizeof(int); }
+
+cudaError_t setup_spin_kernel_attributes(size_t smem_bytes) {
+    static size_t done = 0;
+    if (smem_bytes <= done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(spin_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(spin_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e == cudaSuccess) done = smem_bytes;
+    return e;
+}
+
+int blocks_per_sm_for(size_t smem_bytes) {
+    int n = 0;
+    if (setup_spin_kernel_attributes(smem_bytes) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spin_kernel<false>, kThreads, smem_bytes) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+void launch_spin_kernel(const LaunchArgs &a, int blocks, size_t smem, cudaStream_t stream) {
+    if (a.probe)
+        spin_kernel<true><<<blocks, kThreads, smem, stream>>>(a);
+    else
+        spin_kernel<false><<<blocks, kThreads, smem, stream>>>(a);
+}
+
+// Largest group (power of two, <= 32, or the requested one) whose images fit
+// next to the fixed shared-memory layout with two blocks per SM (one block
+// per SM for the widest images).
+int choose_log2_group(int W, int requested_group) {
+    if (requested_group > 0) {
+        int l = 0;
+        while ((1 << l) < requested_group && l < 5) ++l;
+        return l;
+    }
+    const size_t budget = (size_t)113 * 1024;
+    for (int l = 5; l > 0; --l)
+        if (spin_smem_bytes(image_words(W, l)) <= budget) return l;
+    return 0;
+}
+
+}  // namespace si
