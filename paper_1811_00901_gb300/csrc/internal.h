@@ -133,6 +133,9 @@ int num_sms(int device);
 // Chunk rules (host side, one implementation for every caller).
 int64_t chunk_table(int kind, int64_t units, int workers, int min_chunk, std::vector<int64_t> *starts);
 
+// Synchronous argument checks of one item.
+si_status check_item(const si_batch_item &it, const si_schedule &sc, int dev);
+
 // Enqueue the generation of a batch of items (host-validated) on `stream`.
 si_status enqueue_batch(const std::vector<si_batch_item> &items, const std::vector<si_schedule> &scheds,
                         const std::vector<const si_probe *> &probes, cudaStream_t stream,
