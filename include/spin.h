@@ -175,6 +175,26 @@ si_status si_generate_host(const float *points, const float *normals, int64_t n,
                            float cos_support_angle, si_schedule schedule, int32_t *out,
                            si_stream stream);
 
+/* si_generate_noalloc -- si_generate for callers that must not allocate
+ * device memory during the call.  The paper has no counterpart: it exists for
+ * callers whose device memory is fully reserved by another allocator, or
+ * whose loop runs with a fixed memory footprint and may not enter an
+ * allocator, which si_generate's per-call scratch (from the stream-ordered
+ * pool) and its on-demand grid build would do.
+ *   Arguments, output and results are those of si_generate (images bit-
+ *   identical); explicit query lists are processed in the order given.
+ *   Scratch: one static 2 MiB device array in the library (held by every GPU
+ *   that loads it until exit), enough for 100,000 scheduling steps; a call
+ *   needing more steps is SI_ERR_INVALID (raise min_chunk or group).
+ *   The mesh's grid for this W, bin size and grid_div must exist already
+ *   (si_mesh_prepare); otherwise SI_ERR_INVALID.
+ *   The first call on a device (with it current) looks up the array's device
+ *   address; make that first call before any stream capture.
+ *   Calls share the array: two calls whose work overlaps on the GPU race. */
+si_status si_generate_noalloc(si_mesh_t mesh, const int32_t *query_idx, int64_t m, int32_t W,
+                              float bin_size, float cos_support_angle, si_schedule schedule,
+                              int32_t *out, si_stream stream);
+
 /* ------------------------------------------------------------ scheduling --
  * si_chunk_table -- the chunk boundaries a rule hands out for `units`
  * iterations and `workers` workers (Algorithm 3's getChunk run to the end):

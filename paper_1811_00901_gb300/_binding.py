@@ -61,7 +61,9 @@ _SIGNATURES = {
                             ctypes.c_int),
     "si_generate_host": ([_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_float,
                           ctypes.c_float, si_schedule, _P, _P], ctypes.c_int),
-    "si_chunk_table": ([ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+    "si_generate_noalloc": ([_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_float, si_schedule,
+                             _P, _P], ctypes.c_int),
+    "si_chunk_table":([ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                         ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)],
                        ctypes.c_int),
     "si_candidate_rc2": ([ctypes.c_int32, ctypes.c_float], ctypes.c_float),
@@ -194,6 +196,12 @@ def si_generate_host(points, normals, n, query_idx, m, W, bin_size, cos_s, sched
     """All buffers are host pointers / CPU tensors (pinned is fastest)."""
     _check(load().si_generate_host(_ptr(points), _ptr(normals), int(n), _ptr(query_idx), int(m), int(W),
                                    float(bin_size), float(cos_s), schedule, _ptr(out), _stream_ptr(stream)))
+
+
+def si_generate_noalloc(mesh, query_idx, m, W, bin_size, cos_s, schedule, out, stream=None):
+    """si_generate without any device allocation (static scratch; grid prepared beforehand)."""
+    _check(load().si_generate_noalloc(mesh, _ptr(query_idx), int(m), int(W), float(bin_size), float(cos_s),
+                                      schedule, _ptr(out), _stream_ptr(stream)))
 
 
 def si_chunk_table(kind, units, workers, min_chunk=1):
