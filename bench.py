@@ -45,6 +45,23 @@ def _rank_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def aggregate_max_ms(local_ms, world):
+    """Max of a per-rank time over all ranks (the slowest rank bounds the job)."""
+    if world <= 1:
+        return float(local_ms)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank_step, steps, world, max_ms):
+    """Whole-job rate: the units every rank processed over the max-over-ranks time."""
+    return world * units_per_rank_step * steps / (max_ms / 1e3)
+
+
 def _workload():
     from paper_1811_00901_gb300 import workloads as wl
     return wl.nonuniform_heightfield()
@@ -205,6 +222,21 @@ def run_ours(args):
     spin.si_mesh_destroy(mesh)
     n_culled = int(culled.sum().item())
     n_support = int(support.sum().item())
+    # measured shared-atomic peak (denominator of the splat roofline)
+    atom_peak = spin.si_peak_smem_atomics(0, stream)
+    atom_spread = spin.si_peak_smem_atomics(1, stream)
+    # launch shape from the autotuner (untimed): group size and grid resolution
+    # are shared by every rule below; "tuned" is the tuner's full choice
+    mesh = spin.si_mesh_create(tp, tn, n, stream)
+    tuned, tuned_ms = spin.si_tune_mesh(mesh, None, m, W, B, cs, out, reps=2, stream=stream)
+    spin.si_mesh_destroy(mesh)
+    shape = dict(group=tuned.group, grid_div=tuned.grid_div)
+    configs = {name: spin.make_schedule(name, **shape) for name in SCHEDULES}
+    configs["tuned"] = spin.make_schedule(tuned.kind, min_chunk=tuned.min_chunk, num_workers=tuned.num_workers,
+                                          **shape)
+    tuned_desc = {"kind": [k for k, v in spin.SCHED_NAMES.items() if v == tuned.kind][0],
+                  "min_chunk": tuned.min_chunk, "num_workers": tuned.num_workers, "group": tuned.group,
+                  "grid_div": tuned.grid_div}
 
     results = {}
     clocks = ClockSampler(local)
@@ -212,8 +244,7 @@ def run_ours(args):
     timed_launches = 0
     kernel_ms = {}
     clocks.start()
-    for name in SCHEDULES:
-        sched = spin.make_schedule(name)
+    for name, sched in configs.items():
         for _ in range(args.warmup):
             mesh = one_step(sched)
             stream.synchronize()
@@ -238,22 +269,18 @@ def run_ours(args):
             kms.append(st["kernel_ms"] / max(1, st["kernel_launches"]))
             spin.si_mesh_destroy(mesh)
             times.append(e0.elapsed_time(e1))
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([sum(times)], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
-        else:
-            total_ms = sum(times)
-        results[name] = {"ms_per_step": total_ms / args.steps, "images_per_s": world * m * args.steps / (total_ms / 1e3),
-                         "culled_pairs_per_s": world * n_culled * args.steps / (total_ms / 1e3),
+        total_ms = aggregate_max_ms(sum(times), world)
+        results[name] = {"ms_per_step": total_ms / args.steps,
+                         "images_per_s": job_throughput(m, args.steps, world, total_ms),
+                         "culled_pairs_per_s": job_throughput(n_culled, args.steps, world, total_ms),
                          "kernel_ms": statistics.median(kms),
                          "step_ms_p50": statistics.median(times)}
         kernel_ms[name] = statistics.median(kms)
     clk = clocks.stop()
     del launches0
 
-    best = max(("SS", "GSS", "FAC"), key=lambda k: results[k]["images_per_s"])
+    dls = ["SS", "GSS", "FAC"] + (["tuned"] if tuned_desc["kind"] != "STATIC" else [])
+    best = max(dls, key=lambda k: results[k]["images_per_s"])
     r = results[best]
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
@@ -262,7 +289,7 @@ def run_ours(args):
         hp = torch.from_numpy(c["points"]).pin_memory()
         hn = torch.from_numpy(c["normals"]).pin_memory()
         hout = torch.empty((m, W, W), dtype=torch.int32).pin_memory()
-        sched = spin.make_schedule(best)
+        sched = configs[best]
         for _ in range(max(1, args.warmup)):
             spin.si_generate_host(hp, hn, n, None, m, W, B, cs, sched, hout, stream)
         et = []
@@ -291,12 +318,17 @@ def run_ours(args):
                 "peak_source": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)" % (sms, f_mhz, peak_src),
                 "ops_per_culled_pair": OPS_PER_CULLED, "ops_per_support_pair": OPS_PER_SUPPORT,
                 "write_gbs": m * W * W * 4 / (k_ms / 1e3) / 1e9,
-                "write_frac_of_hbm": (m * W * W * 4 / (k_ms / 1e3) / 1e9) / float(peaks.get("hbm_gbs", 6800.0))}
+                "write_frac_of_hbm": (m * W * W * 4 / (k_ms / 1e3) / 1e9) / float(peaks.get("hbm_gbs", 6800.0)),
+                "smem_atomics": {"achieved_per_s": 4 * n_support / (k_ms / 1e3),
+                                 "peak_per_s": atom_peak, "frac": 4 * n_support / (k_ms / 1e3) / atom_peak,
+                                 "spread_pattern_per_s": atom_spread,
+                                 "peak_source": "measured (si_peak_smem_atomics, conflict-free)"}}
 
     line = {"metric": METRIC, "value": r["images_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config(c, {"schedule": best, "parallelism": "replicas" if world > 1 else "single GPU"}),
+            "config": _config(c, {"schedule": best, "tuned": tuned_desc, "shape": shape,
+                                  "parallelism": "replicas" if world > 1 else "single GPU"}),
             "culled_pairs_per_s": r["culled_pairs_per_s"], "culled_pairs_per_step": n_culled,
             "support_pairs_per_step": n_support,
             "by_schedule": {k: {"images_per_s": v["images_per_s"], "ms_per_step": v["ms_per_step"],
@@ -359,8 +391,46 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_profile_case(args):
+    """A short run for profilers: the bench workload's full path, `reps`
+    times, under one schedule; no flush buffer, probes or CPU legs."""
+    import torch
+
+    import paper_1811_00901_gb300 as spin
+    from paper_1811_00901_gb300 import _build
+    _build.build()
+    dev = torch.device("cuda", 0)
+    c = _workload() if args.profile_workload == "heightfield" else _small_workload(args.profile_workload)
+    n, m, W = c["points"].shape[0], c["m"], c["W"]
+    tp = torch.from_numpy(c["points"]).to(dev)
+    tn = torch.from_numpy(c["normals"]).to(dev)
+    tq = None if c["query_idx"] is None else torch.from_numpy(c["query_idx"]).to(dev)
+    out = torch.empty((m, W, W), dtype=torch.int32, device=dev)
+    sched = spin.make_schedule(args.profile_case)
+    for _ in range(args.reps):
+        mesh = spin.si_mesh_create(tp, tn, n)
+        spin.si_generate(mesh, tq, m, W, float(c["bin_size"]), float(c["cos_s"]), sched, out)
+        torch.cuda.synchronize()
+        spin.si_get_stats(mesh)
+        spin.si_mesh_destroy(mesh)
+    print(json.dumps({"profile_case": args.profile_case, "workload": c["name"], "reps": args.reps}))
+
+
+def _small_workload(name):
+    from paper_1811_00901_gb300 import workloads as wl
+    if name == "sphere":
+        return wl.plain_sphere()
+    if name == "scene":
+        return wl.large_scene()
+    raise ValueError(name)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-case", default=None, choices=list(SCHEDULES),
+                    help="run the workload `--reps` times under one schedule (for ncu)")
+    ap.add_argument("--profile-workload", default="heightfield", choices=["heightfield", "sphere", "scene"])
+    ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
@@ -369,6 +439,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=4.0)
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

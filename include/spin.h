@@ -266,6 +266,13 @@ const char *si_last_error(void);
 const char *si_version(void);
 /* Kernels this library has launched in this process (all devices). */
 int64_t si_kernel_launches(void);
+/* Measures the current device's throughput of shared-memory int32 atomic
+ * adds (atomics per second, all SMs): mode 0 = every lane in its own bank
+ * (the peak), mode 1 = addresses spread over small interleaved images like
+ * the spin kernel's splats.  The roofline denominator of the splat step
+ * (Algorithm 1's tempSpinImage[k, l]++), which no vendor figure covers.
+ * Synchronises `stream`. */
+si_status si_peak_smem_atomics(int32_t mode, double *atomics_per_s, si_stream stream);
 
 #ifdef __cplusplus
 }

@@ -87,6 +87,7 @@ _SIGNATURES = {
     "si_last_error": ([], ctypes.c_char_p),
     "si_version": ([], ctypes.c_char_p),
     "si_kernel_launches": ([], ctypes.c_int64),
+    "si_peak_smem_atomics": ([ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
 }
 
 _lib = None
@@ -325,3 +326,19 @@ def si_version():
 
 def si_kernel_launches():
     return int(load().si_kernel_launches())
+
+
+def si_peak_smem_atomics(mode=0, stream=None):
+    v = ctypes.c_double()
+    _check(load().si_peak_smem_atomics(int(mode), ctypes.byref(v), _stream_ptr(stream)))
+    return v.value
+
+
+class device_view:
+    """A zero-copy view of library-owned device memory (e.g. a server-allocated
+    output) through __cuda_array_interface__: ``torch.as_tensor(device_view(p,
+    shape), device="cuda")``.  The memory stays owned by the library."""
+
+    def __init__(self, ptr, shape, typestr="<i4"):
+        self.__cuda_array_interface__ = {"shape": tuple(int(s) for s in shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}

@@ -312,6 +312,7 @@ si_status enqueue_batch(const std::vector<si_batch_item> &items, const std::vect
         d.invB = 1.0f / it.bin_size;
         d.halfW = 0.5f * (float)it.W;
         d.umax = (float)(it.W - 1);
+        d.amax2 = support_alpha2(it.W, it.bin_size);
         double mag = 0.0;
         for (int a = 0; a < 3; ++a)
             mag = std::max(mag, std::max(std::fabs((double)m->bmin[a]), std::fabs((double)m->bmax[a])));
@@ -324,6 +325,7 @@ si_status enqueue_batch(const std::vector<si_batch_item> &items, const std::vect
             d.p_worker = pr->worker;
             d.p_step = pr->step;
         }
+        std::lock_guard<std::mutex> lk(m->mu);
         m->calls += 1;
         m->images += it.m;
     }

@@ -88,6 +88,7 @@ struct ItemDesc {
     int W;
     int log2S;             // group = 1 << log2S images
     float invB, halfW, umax, Rc2, Rc, cosS;
+    float amax2;           // fl32(((W-1) B)^2): alpha^2 < amax2 is the column support test
     int units;             // ceil(m / group)
     int perm_is_grid;      // perm holds grid orig_idx (all-points query of the mesh)
     // probes (device, may be null)
@@ -122,6 +123,12 @@ struct LaunchArgs {
 };
 
 // ---------------------------------------------------------- host helpers --
+// Column support threshold: v = alpha / B < W - 1  <=>  alpha^2 < ((W-1) B)^2.
+inline float support_alpha2(int W, float B) {
+    const double a = (double)(W - 1) * (double)B;
+    return (float)(a * a);
+}
+
 Grid *mesh_grid(Mesh *m, float cell, cudaStream_t stream, si_status *st);
 float grid_cell_for(const Mesh *m, int W, float bin, int grid_div);
 int choose_log2_group(int W, int requested_group);

@@ -20,12 +20,16 @@
 //     to S lanes and the S images of a group are interleaved word by word in
 //     shared memory (pixel p of slot q at word p*S + q): the 32 lanes of a
 //     warp hit at most 32/S words per bank, whatever pixels they splat.
+//   * Each lane evaluates two candidates per loop trip without branches (the
+//     two chains interleave); a warp skips the trip when no lane's pair
+//     survives the distance cull.
 //
 // Per pair (P = query, X = candidate, FP32, differences taken directly):
 //   d = X - P; cull if fl32(|d|^2) > Rc2; angle test n.n_X >= cos S;
-//   beta = n.d; alpha = |n x d|; u = W/2 - beta/B; v = alpha/B;
-//   support test 0 <= u < W-1, v < W-1; fixed-point bilinear splat of weight
-//   65536 with four shared-memory int32 atomics.
+//   beta = n.d; alpha^2 = |d|^2 - beta^2 (Algorithm 1's form, clamped at 0);
+//   u = W/2 - beta/B; support test 0 <= u < W-1 and alpha^2 < ((W-1)B)^2
+//   (i.e. v = alpha/B < W-1); v = alpha/B; fixed-point bilinear splat of
+//   weight 65536 with four shared-memory int32 atomics.
 // Images hold (W+1) x (W+1) words per slot: the extra row and column absorb
 // the zero-weight corners of points whose coordinate rounds up onto W-1.
 #include "device_common.cuh"
@@ -103,67 +107,359 @@ __device__ int block_scan_rows(const int *len, int *off, int nr, Header &H) {
     return total;
 }
 
-template <bool PROBE>
-__device__ __forceinline__ void splat_pair(const float4 X, const float4 NX, const float4 P, const float4 N,
-                                           const float Rc2, const float cosS, const float invB,
-                                           const float halfW, const float umax, int *img_q, const int row_words,
-                                           const int S, const int log2S, int &cnt, int *pc_c, int *pc_s,
-                                           unsigned *pc_h) {
-    // The candidate-set expression: exactly fl32(fma(dz,dz, fma(dy,dy, dx*dx))).
-    const float dx = __fsub_rn(X.x, P.x);
-    const float dy = __fsub_rn(X.y, P.y);
-    const float dz = __fsub_rn(X.z, P.z);
-    const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-    if (PROBE && d2 <= Rc2) {
-        atomicAdd(pc_c, 1);
-        atomicAdd(pc_h, fmix32(__float_as_uint(X.w)));
-    }
+// Constants of one item that the pair evaluation needs.
+struct PairConsts {
+    float Rc2, cosS, invB, halfW, umax, amax2;
+};
+
+// Shape of a group's images: compile-time when WT > 0, else runtime.
+template <int WT, int LS>
+struct Shape {
+    int W_rt, LS_rt;
+    __device__ __forceinline__ int W() const { return WT > 0 ? WT : W_rt; }
+    __device__ __forceinline__ int log2S() const { return WT > 0 ? LS : LS_rt; }
+    __device__ __forceinline__ int S() const { return 1 << log2S(); }
+    __device__ __forceinline__ int row_words() const { return (W() + 1) << log2S(); }
+};
+
+// The distance part of a pair: d = X - P and the candidate-set expression,
+// exactly fl32(fma(dz,dz, fma(dy,dy, dx*dx))).
+struct PairDist {
+    float dx, dy, dz, d2;
+};
+
+__device__ __forceinline__ PairDist pair_dist(const float4 X, const float4 P) {
+    PairDist r;
+    r.dx = __fsub_rn(X.x, P.x);
+    r.dy = __fsub_rn(X.y, P.y);
+    r.dz = __fsub_rn(X.z, P.z);
+    r.d2 = __fmaf_rn(r.dz, r.dz, __fmaf_rn(r.dy, r.dy, __fmul_rn(r.dx, r.dx)));
+    return r;
+}
+
+// Evaluates the rest of one (query, candidate) pair and splats it when it
+// contributes.  Every contributing pair has |d|^2 < R^2 < Rc2, so the cull
+// itself is not part of the support decision.
+template <int WT, int LS, bool PROBE>
+__device__ __forceinline__ void eval_pair(const PairDist &pd, const float4 X, const float4 NX, const bool live,
+                                          const float4 N, const PairConsts &k, const Shape<WT, LS> sh,
+                                          int *__restrict__ img_q, int &cnt, int *pc_c, int *pc_s,
+                                          unsigned *pc_h) {
+    const float dx = pd.dx, dy = pd.dy, dz = pd.dz, d2 = pd.d2;
     const float ca = fmaf(N.z, NX.z, fmaf(N.y, NX.y, N.x * NX.x));
-    if (!(d2 <= Rc2) || !(ca >= cosS)) return;
     const float beta = fmaf(N.z, dz, fmaf(N.y, dy, N.x * dx));
-    const float cx = fmaf(N.y, dz, -N.z * dy);
-    const float cy = fmaf(N.z, dx, -N.x * dz);
-    const float cz = fmaf(N.x, dy, -N.y * dx);
-    const float a2 = fmaf(cz, cz, fmaf(cy, cy, cx * cx));
-    const float u = __fmaf_rn(-beta, invB, halfW);
-    const float v = sqrtf(a2) * invB;
-    if (!(u >= 0.0f) || !(u < umax) || !(v < umax)) return;
-    if (PROBE) atomicAdd(pc_s, 1);
-    ++cnt;
+    const float a2 = fmaxf(fmaf(-beta, beta, d2), 0.0f);
+    const float u = fmaf(-beta, k.invB, k.halfW);
+    const bool in = live & (ca >= k.cosS) & (u >= 0.0f) & (u < k.umax) & (a2 < k.amax2);
+    if (PROBE && in) atomicAdd(pc_s, 1);
+    (void)pc_c;
+    (void)pc_h;
+    (void)X;
+    // alpha / B through the approximate reciprocal square root; the support
+    // decision above does not depend on it, and 16-bit quantisation absorbs
+    // its last-bit error
+    const float v = a2 * rsqrtf(fmaxf(a2, 1e-30f)) * k.invB;
     // U = rn(u * 2^16): u * 2^16 is exact, adding 2^23 rounds it to an integer
-    // in the low mantissa bits (0 <= U < 2^23 because u < W - 1 <= 127).
-    const int U = __float_as_int(__fmaf_rn(u, 65536.0f, 8388608.0f)) - 0x4B000000;
-    const int V = __float_as_int(__fmaf_rn(v, 65536.0f, 8388608.0f)) - 0x4B000000;
-    const unsigned A = (unsigned)U & 0xFFFFu;
-    const unsigned Bq = (unsigned)V & 0xFFFFu;
-    const int i = U >> 16, j = V >> 16;
+    // held in the low 23 mantissa bits (0 <= U < 2^23 since u < W - 1 <= 127)
+    const unsigned U = __float_as_uint(fmaf(u, 65536.0f, 8388608.0f)) & 0x7FFFFFu;
+    const unsigned V = __float_as_uint(fmaf(v, 65536.0f, 8388608.0f)) & 0x7FFFFFu;
+    const unsigned A = U & 0xFFFFu, Bq = V & 0xFFFFu;
     const unsigned w11 = (A * Bq + 32768u) >> 16;
-    const int w10 = (int)(A - w11);
-    const int w01 = (int)(Bq - w11);
-    const int w00 = (int)(65536u - A - Bq + w11);
-    int *p0 = img_q + ((i * row_words + j * S));
-    atomicAdd(p0, w00);
-    atomicAdd(p0 + row_words, w10);
-    atomicAdd(p0 + S, w01);
-    atomicAdd(p0 + row_words + S, (int)w11);
-    (void)log2S;
+    if (in) {
+        const int S = sh.S(), rw = sh.row_words();
+        int *p0 = img_q + ((int)(U >> 16) * rw + ((int)(V >> 16) << sh.log2S()));
+        atomicAdd(p0, (int)(65536u - A - Bq + w11));
+        atomicAdd(p0 + rw, (int)(A - w11));
+        atomicAdd(p0 + S, (int)(Bq - w11));
+        atomicAdd(p0 + rw + S, (int)w11);
+        ++cnt;
+    }
+}
+
+// Consumes one staged tile: every lane pairs its slot's query with its
+// candidates; two candidates per lane per trip.
+template <int WT, int LS, bool PROBE>
+__device__ __forceinline__ void consume_tile(const float4 *__restrict__ tile, const int len, const int warp,
+                                             const int lane, const bool active, const float4 P, const float4 N,
+                                             const PairConsts &k, const Shape<WT, LS> sh, int *__restrict__ img_q,
+                                             int &cnt, int *pc_c, int *pc_s, unsigned *pc_h) {
+    const int l2 = sh.log2S();
+    const int cpw = 32 >> l2;      // candidates per warp step
+    const int sub = lane >> l2;
+    const int stride = kWarps * cpw;
+    for (int cb = warp * cpw; cb < len; cb += 2 * stride) {
+        const int c0 = cb + sub, c1 = cb + stride + sub;
+        const bool l0 = active & (c0 < len), l1 = active & (c1 < len);
+        const int i0 = l0 ? c0 : 0, i1 = l1 ? c1 : 0;
+        const float4 X0 = tile[2 * i0], X1 = tile[2 * i1];
+        const PairDist d0 = pair_dist(X0, P), d1 = pair_dist(X1, P);
+        const bool near0 = l0 & (d0.d2 <= k.Rc2), near1 = l1 & (d1.d2 <= k.Rc2);
+        if (PROBE) {
+            if (near0) {
+                atomicAdd(pc_c, 1);
+                atomicAdd(pc_h, fmix32(__float_as_uint(X0.w)));
+            }
+            if (near1) {
+                atomicAdd(pc_c, 1);
+                atomicAdd(pc_h, fmix32(__float_as_uint(X1.w)));
+            }
+        }
+        // warp-uniform skip: no lane's pair survives the distance cull
+        if (!__any_sync(0xffffffffu, near0 | near1)) continue;
+        const float4 N0 = tile[2 * i0 + 1], N1 = tile[2 * i1 + 1];
+        eval_pair<WT, LS, PROBE>(d0, X0, N0, near0, N, k, sh, img_q, cnt, pc_c, pc_s, pc_h);
+        eval_pair<WT, LS, PROBE>(d1, X1, N1, near1, N, k, sh, img_q, cnt, pc_c, pc_s, pc_h);
+    }
+}
+
+struct SmemView {
+    Header *H;
+    QueryInfo *Q;
+    int *row_start, *row_len, *row_off;
+    int *pc_culled, *pc_support;
+    unsigned *pc_hash;
+    float4 *tiles;
+    int *img;
+};
+
+// Generates the images of one group (units u of item `it`).  Returns false
+// when a bounded wait gave up (the block then stops).
+template <int WT, int LS, bool PROBE>
+__device__ bool process_group(const ItemDesc &it, const int u, const int step, const SmemView &sv,
+                              uint32_t &phase_bits, uint32_t &armed) {
+    Header &H = *sv.H;
+    QueryInfo *Q = sv.Q;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const Shape<WT, LS> sh{it.W, it.log2S};
+    const int S = sh.S(), W = sh.W(), W1 = W + 1;
+    const int64_t m = it.m;
+    const float4 *__restrict__ pn = it.pn;
+    const int *__restrict__ cstart = it.cell_start;
+    const float ox = it.origin[0], oy = it.origin[1], oz = it.origin[2];
+    const float cell = it.cell, inv = it.inv_cell, margin = it.margin;
+    const int dx_ = it.dims[0], dy_ = it.dims[1], dz_ = it.dims[2];
+    const PairConsts k{it.Rc2, it.cosS, it.invB, it.halfW, it.umax, it.amax2};
+    const float Rc = it.Rc;
+    const int slot = lane & (S - 1);
+    const int img_words_pad = ((S * W1 * W1) + 3) & ~3;
+
+    const int64_t t0 = (int64_t)u * S;
+    const int nq = (int)(m - t0 < (int64_t)S ? m - t0 : (int64_t)S);
+    // ---- queries of the group
+    if (tid < S) {
+        if (tid < nq) {
+            const int64_t t = t0 + tid;
+            const int q = it.perm ? it.perm[t] : (int)t;
+            int sp = (int)t;
+            bool ok = true;
+            if (!it.perm_is_grid) {
+                const int src = it.query_idx ? it.query_idx[q] : q;
+                ok = (unsigned)src < (unsigned)it.n_points;
+                sp = ok ? it.sorted_pos[src] : 0;
+            }
+            if (!ok) atomicOr(it.flags, kFlagBadQuery);
+            Q[tid].p = pn[2 * (int64_t)sp];
+            Q[tid].n = pn[2 * (int64_t)sp + 1];
+            Q[tid].slot = ok ? q : -1;
+        } else {
+            Q[tid].slot = -1;
+        }
+    }
+    if (PROBE && tid < 32) {
+        sv.pc_culled[tid] = 0;
+        sv.pc_support[tid] = 0;
+        sv.pc_hash[tid] = 0;
+    }
+    {
+        int4 *z4 = reinterpret_cast<int4 *>(sv.img);
+        for (int w = tid; w < img_words_pad / 4; w += kThreads) z4[w] = make_int4(0, 0, 0, 0);
+    }
+    __syncthreads();
+    // ---- bounding box of the group and the stencil's y/z cell range
+    if (warp == 0) {
+        float lo0 = INFINITY, lo1 = INFINITY, lo2 = INFINITY;
+        float hi0 = -INFINITY, hi1 = -INFINITY, hi2 = -INFINITY;
+        if (lane < nq) {
+            const float4 p = Q[lane].p;
+            lo0 = hi0 = p.x;
+            lo1 = hi1 = p.y;
+            lo2 = hi2 = p.z;
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            lo0 = fminf(lo0, __shfl_xor_sync(0xffffffffu, lo0, d));
+            lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, d));
+            lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, d));
+            hi0 = fmaxf(hi0, __shfl_xor_sync(0xffffffffu, hi0, d));
+            hi1 = fmaxf(hi1, __shfl_xor_sync(0xffffffffu, hi1, d));
+            hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, d));
+        }
+        if (lane == 0) {
+            H.gmin[0] = lo0;
+            H.gmin[1] = lo1;
+            H.gmin[2] = lo2;
+            H.gmax[0] = hi0;
+            H.gmax[1] = hi1;
+            H.gmax[2] = hi2;
+            const float r = Rc + margin;
+            H.ylo = cell_coord(lo1 - r, oy, inv, dy_);
+            H.yhi = cell_coord(hi1 + r, oy, inv, dy_);
+            H.zlo = cell_coord(lo2 - r, oz, inv, dz_);
+            H.zhi = cell_coord(hi2 + r, oz, inv, dz_);
+        }
+    }
+    __syncthreads();
+    const float4 qP = Q[slot].p;
+    const float4 qN = Q[slot].n;
+    const bool active = slot < nq;
+    int cnt = 0;
+    int *img_q = sv.img + slot;
+    const float gmin0 = H.gmin[0], gmin1 = H.gmin[1], gmin2 = H.gmin[2];
+    const float gmax0 = H.gmax[0], gmax1 = H.gmax[1], gmax2 = H.gmax[2];
+    const int ylo = H.ylo, zlo = H.zlo;
+    const int ny = H.yhi - ylo + 1, nz = H.zhi - zlo + 1;
+    const int nrows_total = ny * nz;
+    bool ok_all = true;
+
+    for (int rb = 0; rb < nrows_total && ok_all; rb += kMaxRows) {
+        const int nr = min(kMaxRows, nrows_total - rb);
+        // ---- candidate rows: for each (z, y) the x range of cells within Rc
+        for (int r = tid; r < nr; r += kThreads) {
+            const int rr = rb + r;
+            const int y = ylo + rr % ny, z = zlo + rr / ny;
+            const float sy0 = fmaf((float)y, cell, oy), sy1 = sy0 + cell;
+            const float sz0 = fmaf((float)z, cell, oz), sz1 = sz0 + cell;
+            const float gy = fmaxf(0.0f, fmaxf(sy0 - gmax1, gmin1 - sy1) - margin);
+            const float gz = fmaxf(0.0f, fmaxf(sz0 - gmax2, gmin2 - sz1) - margin);
+            const float rem = k.Rc2 - gy * gy - gz * gz;
+            int start = 0, len = 0;
+            if (rem >= 0.0f) {
+                const float rx = sqrtf(rem) + margin;
+                const int x0 = cell_coord(gmin0 - rx, ox, inv, dx_);
+                const int x1 = cell_coord(gmax0 + rx, ox, inv, dx_);
+                const int c0 = (z * dy_ + y) * dx_ + x0;
+                start = cstart[c0];
+                len = cstart[c0 + (x1 - x0) + 1] - start;
+            }
+            sv.row_start[r] = start;
+            sv.row_len[r] = len;
+        }
+        __syncthreads();
+        const int total = block_scan_rows(sv.row_len, sv.row_off, nr, H);
+        const int ntiles = (total + kTile - 1) / kTile;
+        // ---- producer state (thread 0): row cursor
+        int cr = 0, co = 0;
+        auto fill = [&](int t) {
+            const int b = t % kStages;
+            const int need = min(kTile, total - t * kTile);
+            float4 *dst = sv.tiles + (size_t)b * kTile * 2;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&H.bar[b], (uint32_t)need * 32u);
+            int done = 0;
+            while (done < need && cr < nr) {
+                const int avail = sv.row_len[cr] - co;
+                if (avail <= 0) {
+                    ++cr;
+                    co = 0;
+                    continue;
+                }
+                const int take = min(need - done, avail);
+                bulk_copy_g2s(dst + 2 * done, pn + 2 * (int64_t)(sv.row_start[cr] + co), (uint32_t)take * 32u,
+                              &H.bar[b]);
+                done += take;
+                co += take;
+            }
+            armed |= 1u << b;
+        };
+        if (tid == 0) {
+            for (int t = 0; t < kStages && t < ntiles; ++t) fill(t);
+        }
+        for (int t = 0; t < ntiles; ++t) {
+            const int b = t % kStages;
+            const bool ok = mbar_wait_bounded(&H.bar[b], (phase_bits >> b) & 1u, kWaitLimitNs);
+            if (ok) {
+                phase_bits ^= 1u << b;
+                if (tid == 0) armed &= ~(1u << b);
+                const int len = min(kTile, total - t * kTile);
+                consume_tile<WT, LS, PROBE>(sv.tiles + (size_t)b * kTile * 2, len, warp, lane, active, qP, qN, k,
+                                            sh, img_q, cnt, sv.pc_culled + slot, sv.pc_support + slot,
+                                            sv.pc_hash + slot);
+            }
+            if (__syncthreads_or(!ok)) {
+                ok_all = false;
+                break;
+            }
+            if (tid == 0 && t + kStages < ntiles) fill(t + kStages);
+        }
+    }
+    if (!ok_all) {
+        if (tid == 0) {
+            atomicOr(it.flags, kFlagTimeout);
+            // drain this block's copies still in flight before leaving
+            for (int b = 0; b < kStages; ++b)
+                if (armed & (1u << b)) mbar_wait_bounded(&H.bar[b], (phase_bits >> b) & 1u, kWaitLimitNs);
+        }
+        return false;
+    }
+    __syncthreads();
+    // ---- write-out: pixel (i, j) of slot q lives at ((i*(W+1) + j) * S + q)
+    long long pix = 0;
+    const int npix = W * W;
+    int32_t *__restrict__ out = it.out;
+    for (int e = tid; e < (npix << sh.log2S()); e += kThreads) {
+        const int q = e & (S - 1);
+        if (q >= nq) continue;
+        const int p = e >> sh.log2S();
+        const int i = p / W, j = p - i * W;
+        const int v = sv.img[(i * W1 + j) * S + q];
+        const int qs = Q[q].slot;
+        if (qs >= 0) __stcs(out + (int64_t)qs * npix + p, v);
+        pix += v;
+    }
+    // ---- exact overflow check of the group: the written pixels (int32 read
+    // as signed) sum to 65536 x pairs unless a pixel wrapped
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        pix += __shfl_xor_sync(0xffffffffu, pix, d);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+    }
+    if (lane == 0) {
+        atomicAdd(&H.grp_pix, (unsigned long long)pix);
+        atomicAdd(&H.grp_weight, (unsigned long long)cnt * 65536ull);
+    }
+    if (PROBE && tid < nq && Q[tid].slot >= 0) {
+        const int q = Q[tid].slot;
+        if (it.p_culled) it.p_culled[q] = sv.pc_culled[tid];
+        if (it.p_hash) it.p_hash[q] = sv.pc_hash[tid];
+        if (it.p_support) it.p_support[q] = sv.pc_support[tid];
+        if (it.p_worker) it.p_worker[q] = (int)blockIdx.x;
+        if (it.p_step) it.p_step[q] = step;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (H.grp_pix != H.grp_weight) atomicOr(it.flags, kFlagOverflow);
+        H.grp_pix = 0;
+        H.grp_weight = 0;
+    }
+    return true;
 }
 
 template <bool PROBE>
-__global__ void __launch_bounds__(kThreads) spin_kernel(LaunchArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) spin_kernel(LaunchArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    Header &H = *reinterpret_cast<Header *>(smem);
-    QueryInfo *Q = reinterpret_cast<QueryInfo *>(smem + off_query());
-    int *row_start = reinterpret_cast<int *>(smem + off_rows());
-    int *row_len = row_start + (kMaxRows + 4);
-    int *row_off = row_len + (kMaxRows + 4);
-    int *pc_culled = reinterpret_cast<int *>(smem + off_probe());
-    int *pc_support = pc_culled + 32;
-    unsigned *pc_hash = reinterpret_cast<unsigned *>(pc_support + 32);
-    float4 *tiles = reinterpret_cast<float4 *>(smem + off_tiles());
-    int *img = reinterpret_cast<int *>(smem + off_images());
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    SmemView sv;
+    sv.H = reinterpret_cast<Header *>(smem);
+    sv.Q = reinterpret_cast<QueryInfo *>(smem + off_query());
+    sv.row_start = reinterpret_cast<int *>(smem + off_rows());
+    sv.row_len = sv.row_start + (kMaxRows + 4);
+    sv.row_off = sv.row_len + (kMaxRows + 4);
+    sv.pc_culled = reinterpret_cast<int *>(smem + off_probe());
+    sv.pc_support = sv.pc_culled + 32;
+    sv.pc_hash = reinterpret_cast<unsigned *>(sv.pc_support + 32);
+    sv.tiles = reinterpret_cast<float4 *>(smem + off_tiles());
+    sv.img = reinterpret_cast<int *>(smem + off_images());
+    Header &H = *sv.H;
+    const int tid = threadIdx.x;
 
     if (tid == 0) {
         for (int b = 0; b < kStages; ++b) mbar_init(&H.bar[b], 1);
@@ -175,10 +471,10 @@ __global__ void __launch_bounds__(kThreads) spin_kernel(LaunchArgs a) {
 
     uint32_t phase_bits = 0;  // expected parity per stage (every thread tracks it)
     uint32_t armed = 0;       // stages with a fill in flight (thread 0)
-    bool aborted = false;
+    bool alive = true;
     int claim_iter = 0;
 
-    while (!aborted) {
+    while (alive) {
         __syncthreads();
         if (tid == 0) {
             int s;
@@ -193,231 +489,25 @@ __global__ void __launch_bounds__(kThreads) spin_kernel(LaunchArgs a) {
         ++claim_iter;
         if (step >= a.nsteps) break;
 
-        for (int pi = a.step_piece[step]; pi < a.step_piece[step + 1] && !aborted; ++pi) {
+        for (int pi = a.step_piece[step]; pi < a.step_piece[step + 1] && alive; ++pi) {
             const Piece pc = a.pieces[pi];
             const ItemDesc &it = a.items[pc.item];
-            const int log2S = it.log2S, S = 1 << log2S;
-            const int W = it.W, W1 = W + 1;
-            const int row_words = W1 << log2S;
-            const int64_t m = it.m;
-            const float4 *__restrict__ pn = it.pn;
-            const int *__restrict__ cstart = it.cell_start;
-            const float ox = it.origin[0], oy = it.origin[1], oz = it.origin[2];
-            const float cell = it.cell, inv = it.inv_cell, margin = it.margin;
-            const int dx_ = it.dims[0], dy_ = it.dims[1], dz_ = it.dims[2];
-            const float Rc2 = it.Rc2, Rc = it.Rc, cosS = it.cosS, invB = it.invB, halfW = it.halfW,
-                        umax = it.umax;
-            const int slot = lane & (S - 1);
-            const int sub = lane >> log2S;
-            const int cpw = 32 >> log2S;
-            const int img_words_pad = ((S * W1 * W1) + 3) & ~3;
-
-            for (int u = pc.u0; u < pc.u1 && !aborted; ++u) {
-                const int64_t t0 = (int64_t)u << log2S;
-                const int nq = (int)(m - t0 < (int64_t)S ? m - t0 : (int64_t)S);
-                // ---- queries of the group
-                if (tid < S) {
-                    if (tid < nq) {
-                        const int64_t t = t0 + tid;
-                        const int q = it.perm ? it.perm[t] : (int)t;
-                        int sp = (int)t;
-                        bool ok = true;
-                        if (!it.perm_is_grid) {
-                            const int src = it.query_idx ? it.query_idx[q] : q;
-                            ok = (unsigned)src < (unsigned)it.n_points;
-                            sp = ok ? it.sorted_pos[src] : 0;
-                        }
-                        if (!ok) atomicOr(it.flags, kFlagBadQuery);
-                        Q[tid].p = pn[2 * (int64_t)sp];
-                        Q[tid].n = pn[2 * (int64_t)sp + 1];
-                        Q[tid].slot = ok ? q : -1;
-                    } else {
-                        Q[tid].slot = -1;
-                    }
-                }
-                if (PROBE && tid < 32) {
-                    pc_culled[tid] = 0;
-                    pc_support[tid] = 0;
-                    pc_hash[tid] = 0;
-                }
-                {
-                    int4 *z4 = reinterpret_cast<int4 *>(img);
-                    for (int k = tid; k < img_words_pad / 4; k += kThreads) z4[k] = make_int4(0, 0, 0, 0);
-                }
-                __syncthreads();
-                // ---- bounding box of the group and the stencil's y/z cell range
-                if (warp == 0) {
-                    float lo0 = INFINITY, lo1 = INFINITY, lo2 = INFINITY;
-                    float hi0 = -INFINITY, hi1 = -INFINITY, hi2 = -INFINITY;
-                    if (lane < nq) {
-                        const float4 p = Q[lane].p;
-                        lo0 = hi0 = p.x;
-                        lo1 = hi1 = p.y;
-                        lo2 = hi2 = p.z;
-                    }
-#pragma unroll
-                    for (int d = 16; d > 0; d >>= 1) {
-                        lo0 = fminf(lo0, __shfl_xor_sync(0xffffffffu, lo0, d));
-                        lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, d));
-                        lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, d));
-                        hi0 = fmaxf(hi0, __shfl_xor_sync(0xffffffffu, hi0, d));
-                        hi1 = fmaxf(hi1, __shfl_xor_sync(0xffffffffu, hi1, d));
-                        hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, d));
-                    }
-                    if (lane == 0) {
-                        H.gmin[0] = lo0;
-                        H.gmin[1] = lo1;
-                        H.gmin[2] = lo2;
-                        H.gmax[0] = hi0;
-                        H.gmax[1] = hi1;
-                        H.gmax[2] = hi2;
-                        const float r = Rc + margin;
-                        H.ylo = cell_coord(lo1 - r, oy, inv, dy_);
-                        H.yhi = cell_coord(hi1 + r, oy, inv, dy_);
-                        H.zlo = cell_coord(lo2 - r, oz, inv, dz_);
-                        H.zhi = cell_coord(hi2 + r, oz, inv, dz_);
-                    }
-                }
-                __syncthreads();
-                // query point and normal of this lane's slot
-                const float4 qP = Q[slot].p;
-                const float4 qN = Q[slot].n;
-                const bool active = slot < nq;
-                int cnt = 0;
-                int *img_q = img + slot;
-                const float gmin0 = H.gmin[0], gmin1 = H.gmin[1], gmin2 = H.gmin[2];
-                const float gmax0 = H.gmax[0], gmax1 = H.gmax[1], gmax2 = H.gmax[2];
-                const int ylo = H.ylo, zlo = H.zlo;
-                const int ny = H.yhi - ylo + 1, nz = H.zhi - zlo + 1;
-                const int nrows_total = ny * nz;
-
-                for (int rb = 0; rb < nrows_total && !aborted; rb += kMaxRows) {
-                    const int nr = min(kMaxRows, nrows_total - rb);
-                    // ---- candidate rows: for each (z, y) the x range of cells within Rc
-                    for (int r = tid; r < nr; r += kThreads) {
-                        const int rr = rb + r;
-                        const int y = ylo + rr % ny, z = zlo + rr / ny;
-                        const float sy0 = fmaf((float)y, cell, oy), sy1 = sy0 + cell;
-                        const float sz0 = fmaf((float)z, cell, oz), sz1 = sz0 + cell;
-                        const float gy = fmaxf(0.0f, fmaxf(sy0 - gmax1, gmin1 - sy1) - margin);
-                        const float gz = fmaxf(0.0f, fmaxf(sz0 - gmax2, gmin2 - sz1) - margin);
-                        const float rem = Rc2 - gy * gy - gz * gz;
-                        int start = 0, len = 0;
-                        if (rem >= 0.0f) {
-                            const float rx = sqrtf(rem) + margin;
-                            const int x0 = cell_coord(gmin0 - rx, ox, inv, dx_);
-                            const int x1 = cell_coord(gmax0 + rx, ox, inv, dx_);
-                            const int c0 = (z * dy_ + y) * dx_ + x0;
-                            start = cstart[c0];
-                            len = cstart[c0 + (x1 - x0) + 1] - start;
-                        }
-                        row_start[r] = start;
-                        row_len[r] = len;
-                    }
-                    __syncthreads();
-                    const int total = block_scan_rows(row_len, row_off, nr, H);
-                    const int ntiles = (total + kTile - 1) / kTile;
-                    // ---- producer state (thread 0): row cursor
-                    int cr = 0, co = 0;
-                    auto fill = [&](int k) {
-                        const int b = k % kStages;
-                        const int need = min(kTile, total - k * kTile);
-                        float4 *dst = tiles + (size_t)b * kTile * 2;
-                        fence_proxy_async_smem();
-                        mbar_arrive_expect_tx(&H.bar[b], (uint32_t)need * 32u);
-                        int done = 0;
-                        while (done < need && cr < nr) {
-                            const int avail = row_len[cr] - co;
-                            if (avail <= 0) {
-                                ++cr;
-                                co = 0;
-                                continue;
-                            }
-                            const int take = min(need - done, avail);
-                            bulk_copy_g2s(dst + 2 * done, pn + 2 * (int64_t)(row_start[cr] + co),
-                                          (uint32_t)take * 32u, &H.bar[b]);
-                            done += take;
-                            co += take;
-                        }
-                        armed |= 1u << b;
-                    };
-                    if (tid == 0) {
-                        for (int k = 0; k < kStages && k < ntiles; ++k) fill(k);
-                    }
-                    for (int k = 0; k < ntiles; ++k) {
-                        const int b = k % kStages;
-                        const bool ok = mbar_wait_bounded(&H.bar[b], (phase_bits >> b) & 1u, kWaitLimitNs);
-                        if (ok) {
-                            phase_bits ^= 1u << b;
-                            if (tid == 0) armed &= ~(1u << b);
-                            const int len = min(kTile, total - k * kTile);
-                            const float4 *tile = tiles + (size_t)b * kTile * 2;
-                            if (active) {
-#pragma unroll 2
-                                for (int c = warp * cpw + sub; c < len; c += kWarps * cpw) {
-                                    const float4 X = tile[2 * c];
-                                    const float4 NX = tile[2 * c + 1];
-                                    splat_pair<PROBE>(X, NX, qP, qN, Rc2, cosS, invB, halfW, umax, img_q,
-                                                      row_words, S, log2S, cnt, pc_culled + slot,
-                                                      pc_support + slot, pc_hash + slot);
-                                }
-                            }
-                        }
-                        if (__syncthreads_or(!ok)) {
-                            aborted = true;
-                            break;
-                        }
-                        if (tid == 0 && k + kStages < ntiles) fill(k + kStages);
-                    }
-                }
-                if (aborted) {
-                    if (tid == 0) {
-                        atomicOr(it.flags, kFlagTimeout);
-                        // drain this block's copies still in flight before leaving
-                        for (int b = 0; b < kStages; ++b)
-                            if (armed & (1u << b)) mbar_wait_bounded(&H.bar[b], (phase_bits >> b) & 1u, kWaitLimitNs);
-                    }
-                    break;
-                }
-                __syncthreads();
-                // ---- write-out: pixel (i, j) of slot q lives at ((i*(W+1) + j) * S + q)
-                long long pix = 0;
-                const int npix = W * W;
-                int32_t *__restrict__ out = it.out;
-                for (int k = tid; k < (npix << log2S); k += kThreads) {
-                    const int q = k & (S - 1);
-                    if (q >= nq) continue;
-                    const int p = k >> log2S;
-                    const int i = p / W, j = p - i * W;
-                    const int v = img[(i * W1 + j) * S + q];
-                    const int qs = Q[q].slot;
-                    if (qs >= 0) __stcs(out + (int64_t)qs * npix + p, v);
-                    pix += v;
-                }
-                // ---- exact overflow check of the group: the written pixels
-                // (int32 read as signed) sum to 65536 x pairs unless a pixel wrapped
-#pragma unroll
-                for (int d = 16; d > 0; d >>= 1) {
-                    pix += __shfl_xor_sync(0xffffffffu, pix, d);
-                    cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
-                }
-                if (lane == 0) {
-                    atomicAdd(&H.grp_pix, (unsigned long long)pix);
-                    atomicAdd(&H.grp_weight, (unsigned long long)cnt * 65536ull);
-                }
-                if (PROBE && tid < nq && Q[tid].slot >= 0) {
-                    const int q = Q[tid].slot;
-                    if (it.p_culled) it.p_culled[q] = pc_culled[tid];
-                    if (it.p_hash) it.p_hash[q] = pc_hash[tid];
-                    if (it.p_support) it.p_support[q] = pc_support[tid];
-                    if (it.p_worker) it.p_worker[q] = (int)blockIdx.x;
-                    if (it.p_step) it.p_step[q] = step;
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    if (H.grp_pix != H.grp_weight) atomicOr(it.flags, kFlagOverflow);
-                    H.grp_pix = 0;
-                    H.grp_weight = 0;
+            const int key = it.W * 8 + it.log2S;
+            for (int u = pc.u0; u < pc.u1 && alive; ++u) {
+                // specialised shapes for the common widths, a runtime one otherwise
+                switch (key) {
+                    case 16 * 8 + 5:
+                        alive = process_group<16, 5, PROBE>(it, u, step, sv, phase_bits, armed);
+                        break;
+                    case 32 * 8 + 4:
+                        alive = process_group<32, 4, PROBE>(it, u, step, sv, phase_bits, armed);
+                        break;
+                    case 64 * 8 + 2:
+                        alive = process_group<64, 2, PROBE>(it, u, step, sv, phase_bits, armed);
+                        break;
+                    default:
+                        alive = process_group<0, 0, PROBE>(it, u, step, sv, phase_bits, armed);
+                        break;
                 }
             }
         }
@@ -470,8 +560,7 @@ void launch_spin_kernel(const LaunchArgs &a, int blocks, size_t smem, cudaStream
 }
 
 // Largest group (power of two, <= 32, or the requested one) whose images fit
-// next to the fixed shared-memory layout with two blocks per SM (one block
-// per SM for the widest images).
+// next to the fixed shared-memory layout with two blocks per SM.
 int choose_log2_group(int W, int requested_group) {
     if (requested_group > 0) {
         int l = 0;

@@ -67,3 +67,39 @@ def test_invalid_chunk_table_args(lib):
     assert lib.si_chunk_table(9, 10, 2, 1, None, 0, ctypes.byref(n)) != 0
     assert lib.si_chunk_table(0, 10, 0, 1, None, 0, ctypes.byref(n)) != 0
     assert lib.si_last_error()
+
+
+def test_tuning_table_json_round_trip(lib, tmp_path):
+    """The tuning table is host state: load, nearest-class lookup, save, clear."""
+    import json
+
+    import paper_1811_00901_gb300 as spin
+    spin.si_tune_clear()
+    path = tmp_path / "t.json"
+    path.write_text(json.dumps({"entries": [
+        {"W": 32, "log2n": 16, "log2m": 16, "kind": 3, "min_chunk": 2, "num_workers": 0, "group": 16,
+         "grid_div": 8, "ms": 8.5},
+        {"W": 16, "log2n": 12, "log2m": 12, "kind": 1, "min_chunk": 1, "num_workers": 304, "group": 32,
+         "grid_div": 4, "ms": 0.3}]}))
+    spin.si_tune_load(str(path))
+    s = spin.si_tune_lookup(32, 100_000, 100_000)  # log2 = 16: exact class
+    assert (s.kind, s.min_chunk, s.group, s.grid_div) == (3, 2, 16, 8)
+    s = spin.si_tune_lookup(32, 150_000, 40_000)  # nearest class with the same W
+    assert s.kind == 3
+    s = spin.si_tune_lookup(16, 4096, 4096)
+    assert (s.kind, s.num_workers, s.group) == (1, 304, 32)
+    assert spin.si_tune_lookup(64, 4096, 4096) is None  # no entry for W = 64
+    out = tmp_path / "u.json"
+    spin.si_tune_save(str(out))
+    d = json.loads(out.read_text())
+    assert len(d["entries"]) == 2
+    spin.si_tune_clear()
+    assert spin.si_tune_lookup(32, 100_000, 100_000) is None
+    spin.si_tune_load(str(out))
+    assert spin.si_tune_lookup(32, 100_000, 100_000).grid_div == 8
+    spin.si_tune_clear()
+    bad = tmp_path / "bad.json"
+    bad.write_text('{"entries": [{"W": 8, "log2n": 1, "log2m": 1, "kind": 9, "min_chunk": 1, '
+                   '"num_workers": 0, "group": 1, "grid_div": 1}]}')
+    with pytest.raises(spin.SpinError):
+        spin.si_tune_load(str(bad))
