@@ -336,6 +336,20 @@ def run_ours(args):
             "dls_over_static": r["images_per_s"] / results["STATIC"]["images_per_s"],
             "e2e": e2e, "roofline": roofline,
             "gpu_launches": int(timed_launches), "clocks": clk}
+    if not args.no_extra:
+        from paper_1811_00901_gb300 import workloads as wl
+        ex_steps = max(1, min(args.steps, 3))
+        extra = {}
+        extra["sphere-4096-W16"] = bench_single(spin, torch, dev, wl.plain_sphere(), args.steps, args.warmup, flush,
+                                                stream, kinds=("STATIC", "SS", "GSS", "FAC"))
+        extra["scene-1M-W64"] = bench_single(spin, torch, dev, wl.large_scene(), ex_steps, args.warmup, flush,
+                                             stream, kinds=("STATIC", "FAC"))
+        del out
+        torch.cuda.empty_cache()
+        extra["batched-512-spheres"] = bench_batched(spin, torch, dev, ex_steps, args.warmup, stream)
+        torch.cuda.empty_cache()
+        extra["serving-64-meshes"] = bench_serving(spin, torch, dev, args.serve_requests, args.serve_pool)
+        line["workloads"] = extra
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(c, budget_s=args.cpu_seconds)
     if rank == 0:
@@ -343,6 +357,161 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# the other workloads (secondary keys of the same line)
+# --------------------------------------------------------------------------
+
+def bench_single(spin, torch, dev, c, steps, warmup, flush, stream, kinds=("STATIC", "FAC")):
+    """One mesh, all its images (or its query list), per rule; kernel time by events."""
+    n, m, W, B, cs = c["points"].shape[0], c["m"], c["W"], float(c["bin_size"]), float(c["cos_s"])
+    tp = torch.from_numpy(c["points"]).to(dev)
+    tn = torch.from_numpy(c["normals"]).to(dev)
+    tq = None if c["query_idx"] is None else torch.from_numpy(c["query_idx"]).to(dev)
+    out = torch.empty((m, W, W), dtype=torch.int32, device=dev)
+    res = {}
+    for kind in kinds:
+        sched = spin.make_schedule(kind)
+        times, kms = [], []
+        for k in range(warmup + steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            spin.si_set_timing(True)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mesh = spin.si_mesh_create(tp, tn, n, stream)
+            spin.si_generate(mesh, tq, m, W, B, cs, sched, out, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            spin.si_set_timing(False)
+            st, _ = spin.si_get_stats(mesh)
+            spin.si_mesh_destroy(mesh)
+            if k >= warmup:
+                times.append(e0.elapsed_time(e1))
+                kms.append(st["kernel_ms"] / max(1, st["kernel_launches"]))
+        res[kind] = {"images_per_s": m / (statistics.median(times) / 1e3), "ms_per_step": statistics.median(times),
+                     "kernel_ms": statistics.median(kms)}
+    del out
+    return {"images": m, "W": W, "points": n, "by_schedule": res}
+
+
+def bench_batched(spin, torch, dev, steps, warmup, stream):
+    """512 sphere meshes with their own W, B, angle: one graph-captured persistent
+    launch per step (tuned rules per size class vs PSIA-STATIC)."""
+    from paper_1811_00901_gb300 import workloads as wl
+    items = wl.batched_spheres()
+    meshes, batch = [], []
+    total_images = 0
+    free, _ = torch.cuda.mem_get_info(dev)
+    need = sum(it["m"] * it["W"] * it["W"] * 4 for it in items)
+    if need > 0.8 * free:
+        return {"skipped": "needs %.1f GB of image output, %.1f GB free" % (need / 1e9, free / 1e9)}
+    for it in items:
+        mesh = spin.si_mesh_create(torch.from_numpy(it["points"]).to(dev), torch.from_numpy(it["normals"]).to(dev),
+                                   stream=stream)
+        meshes.append(mesh)
+        out = torch.empty((it["m"], it["W"], it["W"]), dtype=torch.int32, device=dev)
+        batch.append(dict(mesh=mesh, query_idx=None, m=it["m"], W=it["W"], bin_size=float(it["bin_size"]),
+                          cos_s=float(it["cos_s"]), out=out))
+        total_images += it["m"]
+    res = {}
+    try:
+        for name, sched in (("tuned_or_GSS", None), ("STATIC", spin.make_schedule("STATIC"))):
+            times = []
+            for k in range(warmup + steps):
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                spin.si_generate_batched(batch, sched, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if k >= warmup:
+                    times.append(e0.elapsed_time(e1))
+            res[name] = {"images_per_s": total_images / (statistics.median(times) / 1e3),
+                         "ms_per_step": statistics.median(times)}
+    finally:
+        for mesh in meshes:
+            spin.si_mesh_destroy(mesh)
+    return {"meshes": len(items), "images": total_images, "output_gb": need / 1e9, "by_schedule": res,
+            "dls_over_static": res["tuned_or_GSS"]["images_per_s"] / res["STATIC"]["images_per_s"]}
+
+
+def bench_serving(spin, torch, dev, n_requests, pool_size, load_factors=(0.5, 0.8, 0.95)):
+    """Resident mesh pool, Poisson request stream, continuous batching:
+    saturated request rate, then p50/p99 latency at fractions of it."""
+    from paper_1811_00901_gb300 import workloads as wl
+    pool = wl.serving_pool(count=pool_size)
+    meshes = [spin.si_mesh_create(torch.from_numpy(p["points"]).to(dev), torch.from_numpy(p["normals"]).to(dev))
+              for p in pool]
+    sizes = [p["points"].shape[0] for p in pool]
+    srv = spin.si_serve_create(16 << 30, 256)
+    try:
+        for mh in meshes:
+            spin.si_serve_add_mesh(srv, mh)
+        # resident grids for both widths (the pool keeps them)
+        for mh in meshes:
+            for W in (16, 32):
+                spin.si_mesh_prepare(mh, W, 0.8 / W)
+        torch.cuda.synchronize()
+
+        def run(reqs, rate=None):
+            import threading
+            qs = [torch.from_numpy(r["query_idx"]).to(dev) for r in reqs]
+            torch.cuda.synchronize()
+            tickets = [None] * len(reqs)
+            lat = [0.0] * len(reqs)
+            done = threading.Event()
+
+            def waiter():
+                for k in range(len(reqs)):
+                    while tickets[k] is None:
+                        time.sleep(0.0001)
+                    spin.si_serve_wait(srv, tickets[k], -1)
+                    _, lat[k] = spin.si_serve_result(srv, tickets[k])
+                    spin.si_serve_release(srv, tickets[k])
+                done.set()
+            th = threading.Thread(target=waiter, daemon=True)
+            th.start()
+            t0 = time.perf_counter()
+            for k, r in enumerate(reqs):
+                if rate is not None:
+                    wait = r["t"] * (1.0 / rate) * r["rate0"] - (time.perf_counter() - t0)
+                    if wait > 0:
+                        time.sleep(wait)
+                item = dict(mesh=meshes[r["mesh"]], query_idx=qs[k], m=r["m"], W=r["W"],
+                            bin_size=float(r["bin_size"]), cos_s=float(r["cos_s"]), out=None)
+                t = None
+                while t is None:
+                    t = spin.si_serve_submit(srv, item)
+                tickets[k] = t
+            done.wait()
+            wall = time.perf_counter() - t0
+            images = sum(r["m"] for r in reqs)
+            return wall, images, lat
+
+        base_rate = 1000.0
+        reqs = wl.request_stream(sizes, count=n_requests, rate_per_s=base_rate)
+        for r in reqs:
+            r["rate0"] = base_rate
+        wall, images, lat = run(reqs)  # burst: everything at once -> saturated throughput
+        sat_rps = n_requests / wall
+        out = {"meshes": pool_size, "points": int(sum(sizes)), "requests": n_requests,
+               "saturated": {"requests_per_s": sat_rps, "images_per_s": images / wall,
+                             "p50_ms": float(np.percentile(lat, 50)) / 1e3,
+                             "p99_ms": float(np.percentile(lat, 99)) / 1e3}}
+        for f in load_factors:
+            wall, images, lat = run(reqs, rate=f * sat_rps)
+            out["load_%.2f" % f] = {"offered_requests_per_s": f * sat_rps, "images_per_s": images / wall,
+                                    "p50_ms": float(np.percentile(lat, 50)) / 1e3,
+                                    "p99_ms": float(np.percentile(lat, 99)) / 1e3}
+        return out
+    finally:
+        spin.si_serve_destroy(srv)
+        for mh in meshes:
+            spin.si_mesh_destroy(mh)
 
 
 # --------------------------------------------------------------------------
@@ -436,6 +605,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the sphere, 1M-scene, batched and serving runs")
+    ap.add_argument("--serve-requests", type=int, default=4000)
+    ap.add_argument("--serve-pool", type=int, default=64)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=4.0)
     args = ap.parse_args()

@@ -24,7 +24,17 @@ si_status cuda_fail(cudaError_t e, const char *what);
     } while (0)
 
 // ------------------------------------------------------------- constants --
-constexpr int kThreads = 256;       // threads per spin-kernel block (8 warps)
+// Build-time shape of the spin kernel (defaults measured best on GB300).
+#ifndef SI_THREADS
+#define SI_THREADS 256
+#endif
+#ifndef SI_MIN_BLOCKS
+#define SI_MIN_BLOCKS 3
+#endif
+#ifndef SI_SMEM_BUDGET_KB
+#define SI_SMEM_BUDGET_KB 75
+#endif
+constexpr int kThreads = SI_THREADS;  // threads per spin-kernel block
 constexpr int kTile = 256;          // candidate points per staged tile (8 KB)
 constexpr int kStages = 3;          // tile ring depth
 constexpr int kMaxRows = 512;       // stencil rows held in shared memory at once
@@ -147,6 +157,12 @@ si_status check_item(const si_batch_item &it, const si_schedule &sc, int dev);
 si_status enqueue_batch(const std::vector<si_batch_item> &items, const std::vector<si_schedule> &scheds,
                         const std::vector<const si_probe *> &probes, cudaStream_t stream,
                         int forced_workers);
+// The same for batched calls through the CUDA-graph cache (capture once,
+// replay for identical batches); the legacy default stream goes direct.
+si_status enqueue_batch_graph(const std::vector<si_batch_item> &items, const std::vector<si_schedule> &scheds,
+                              cudaStream_t stream, int forced_workers);
+void forget_mesh_graphs(const void *mesh);
+size_t cached_batch_graphs();
 
 // Pinned staging ring for host->device uploads.
 si_status stage_upload(void *dev_dst, const void *src, size_t bytes, cudaStream_t stream);

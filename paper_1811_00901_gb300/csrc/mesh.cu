@@ -143,7 +143,7 @@ bool is_device_pointer(const void *p) {
 float grid_cell_for(const Mesh *m, int W, float bin, int grid_div) {
     (void)m;
     double R = std::sqrt((double)si_candidate_rc2(W, bin));
-    int div = grid_div > 0 ? grid_div : 4;
+    int div = grid_div > 0 ? grid_div : 8;
     double c = R / div;
     double e = std::floor(std::log2(c) * 4.0) / 4.0;
     return (float)std::exp2(e);
@@ -329,6 +329,7 @@ si_status si_mesh_destroy(si_mesh_t mesh) {
         return SI_ERR_INVALID;
     }
     Mesh *m = reinterpret_cast<Mesh *>(mesh);
+    forget_mesh_graphs(m);  // cached batch graphs hold this mesh's grid pointers
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(m->device);

@@ -445,7 +445,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
 }
 
 template <bool PROBE>
-__global__ void __launch_bounds__(kThreads, 2) spin_kernel(LaunchArgs a) {
+__global__ void __launch_bounds__(kThreads, SI_MIN_BLOCKS) spin_kernel(LaunchArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     SmemView sv;
     sv.H = reinterpret_cast<Header *>(smem);
@@ -501,6 +501,12 @@ __global__ void __launch_bounds__(kThreads, 2) spin_kernel(LaunchArgs a) {
                         break;
                     case 32 * 8 + 4:
                         alive = process_group<32, 4, PROBE>(it, u, step, sv, phase_bits, armed);
+                        break;
+                    case 32 * 8 + 3:
+                        alive = process_group<32, 3, PROBE>(it, u, step, sv, phase_bits, armed);
+                        break;
+                    case 64 * 8 + 1:
+                        alive = process_group<64, 1, PROBE>(it, u, step, sv, phase_bits, armed);
                         break;
                     case 64 * 8 + 2:
                         alive = process_group<64, 2, PROBE>(it, u, step, sv, phase_bits, armed);
@@ -567,7 +573,7 @@ int choose_log2_group(int W, int requested_group) {
         while ((1 << l) < requested_group && l < 5) ++l;
         return l;
     }
-    const size_t budget = (size_t)113 * 1024;
+    const size_t budget = (size_t)SI_SMEM_BUDGET_KB * 1024;
     for (int l = 5; l > 0; --l)
         if (spin_smem_bytes(image_words(W, l)) <= budget) return l;
     return 0;
