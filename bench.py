@@ -215,13 +215,15 @@ def run_ours(args):
     mesh = spin.si_mesh_create(tp, tn, n, stream)
     culled = torch.zeros(m, dtype=torch.int64, device=dev)
     support = torch.zeros(m, dtype=torch.int64, device=dev)
+    examined = torch.zeros(m, dtype=torch.int64, device=dev)
     spin.si_generate_probe(mesh, None, m, W, B, cs, sched_probe, out, culled=culled, support=support,
-                           stream=stream)
+                           examined=examined, stream=stream)
     torch.cuda.synchronize()
     spin.si_get_stats(mesh)
     spin.si_mesh_destroy(mesh)
     n_culled = int(culled.sum().item())
     n_support = int(support.sum().item())
+    n_examined = int(examined.sum().item())
     # measured shared-atomic peak (denominator of the splat roofline)
     atom_peak = spin.si_peak_smem_atomics(0, stream)
     atom_spread = spin.si_peak_smem_atomics(1, stream)
@@ -330,7 +332,8 @@ def run_ours(args):
             "config": _config(c, {"schedule": best, "tuned": tuned_desc, "shape": shape,
                                   "parallelism": "replicas" if world > 1 else "single GPU"}),
             "culled_pairs_per_s": r["culled_pairs_per_s"], "culled_pairs_per_step": n_culled,
-            "support_pairs_per_step": n_support,
+            "support_pairs_per_step": n_support, "examined_pairs_per_step": n_examined,
+            "stencil_overhead": n_examined / max(1, n_culled),
             "by_schedule": {k: {"images_per_s": v["images_per_s"], "ms_per_step": v["ms_per_step"],
                                 "kernel_ms": v["kernel_ms"]} for k, v in results.items()},
             "dls_over_static": r["images_per_s"] / results["STATIC"]["images_per_s"],

@@ -92,6 +92,8 @@ typedef struct si_probe {
     int64_t *support;    /* number of contributing X */
     int32_t *worker;     /* thread block that generated the image */
     int32_t *step;       /* scheduling step whose chunk contained the image */
+    int64_t *examined;   /* candidate points the kernel streamed for the image (the grid
+                            stencil; examined / culled is the culling overhead) */
 } si_probe;
 
 typedef struct si_stats {

@@ -291,6 +291,7 @@ void fill_blob(const Plan &p, const std::vector<si_batch_item> &items, const std
             d.p_support = pr->support;
             d.p_worker = pr->worker;
             d.p_step = pr->step;
+            d.p_examined = pr->examined;
         }
     }
     char *h = blob->data();

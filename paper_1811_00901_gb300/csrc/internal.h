@@ -35,8 +35,14 @@ si_status cuda_fail(cudaError_t e, const char *what);
 #define SI_SMEM_BUDGET_KB 75
 #endif
 constexpr int kThreads = SI_THREADS;  // threads per spin-kernel block
-constexpr int kTile = 256;          // candidate points per staged tile (8 KB)
-constexpr int kStages = 3;          // tile ring depth
+#ifndef SI_TILE
+#define SI_TILE 256
+#endif
+#ifndef SI_STAGES
+#define SI_STAGES 3
+#endif
+constexpr int kTile = SI_TILE;      // candidate points per staged tile (32 B each)
+constexpr int kStages = SI_STAGES;  // tile ring depth
 constexpr int kMaxRows = 512;       // stencil rows held in shared memory at once
 constexpr int kMaxW = 128;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // bounded device waits: 2 s
@@ -107,6 +113,7 @@ struct ItemDesc {
     int64_t *p_support;
     int32_t *p_worker;
     int32_t *p_step;
+    int64_t *p_examined;
 };
 
 // A piece of the scheduled loop: units [u0, u1) of item `item`.

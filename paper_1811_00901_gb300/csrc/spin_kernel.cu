@@ -59,11 +59,11 @@ struct __align__(16) Header {
     unsigned long long grp_pix;
 };
 
-constexpr int kHeaderBytes = 256;
+constexpr int kHeaderBytes = (sizeof(Header) + 127) / 128 * 128;
 static_assert(sizeof(Header) <= kHeaderBytes, "header too large");
 constexpr int kQueryBytes = 32 * sizeof(QueryInfo);
 constexpr int kRowBytes = 3 * (kMaxRows + 4) * sizeof(int);
-constexpr int kProbeBytes = 3 * 32 * sizeof(int);
+constexpr int kProbeBytes = 4 * 32 * sizeof(int);
 constexpr int kTileBytes = kStages * kTile * 32;
 
 constexpr int off_query() { return kHeaderBytes; }
@@ -216,7 +216,7 @@ struct SmemView {
     Header *H;
     QueryInfo *Q;
     int *row_start, *row_len, *row_off;
-    int *pc_culled, *pc_support;
+    int *pc_culled, *pc_support, *pc_examined;
     unsigned *pc_hash;
     float4 *tiles;
     int *img;
@@ -269,6 +269,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
         sv.pc_culled[tid] = 0;
         sv.pc_support[tid] = 0;
         sv.pc_hash[tid] = 0;
+        sv.pc_examined[tid] = 0;
     }
     {
         int4 *z4 = reinterpret_cast<int4 *>(sv.img);
@@ -381,6 +382,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
                 phase_bits ^= 1u << b;
                 if (tid == 0) armed &= ~(1u << b);
                 const int len = min(kTile, total - t * kTile);
+                if (PROBE && tid < nq) sv.pc_examined[tid] += len;
                 consume_tile<WT, LS, PROBE>(sv.tiles + (size_t)b * kTile * 2, len, warp, lane, active, qP, qN, k,
                                             sh, img_q, cnt, sv.pc_culled + slot, sv.pc_support + slot,
                                             sv.pc_hash + slot);
@@ -433,6 +435,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
         if (it.p_hash) it.p_hash[q] = sv.pc_hash[tid];
         if (it.p_support) it.p_support[q] = sv.pc_support[tid];
         if (it.p_worker) it.p_worker[q] = (int)blockIdx.x;
+        if (it.p_examined) it.p_examined[q] = sv.pc_examined[tid];
         if (it.p_step) it.p_step[q] = step;
     }
     __syncthreads();
@@ -456,6 +459,7 @@ __global__ void __launch_bounds__(kThreads, SI_MIN_BLOCKS) spin_kernel(LaunchArg
     sv.pc_culled = reinterpret_cast<int *>(smem + off_probe());
     sv.pc_support = sv.pc_culled + 32;
     sv.pc_hash = reinterpret_cast<unsigned *>(sv.pc_support + 32);
+    sv.pc_examined = sv.pc_support + 64;
     sv.tiles = reinterpret_cast<float4 *>(smem + off_tiles());
     sv.img = reinterpret_cast<int *>(smem + off_images());
     Header &H = *sv.H;
