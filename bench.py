@@ -168,11 +168,12 @@ def _ncu_traffic(workload):
 # Algorithmic ALU work, per unit (lane-operations; an FMA counts once):
 #   per culled pair (fl32 |X-P|^2 <= Rc2): difference (3), squared norm (3),
 #   compare (1), normal dot (3), compare (1)                        -> 11
-#   per contributing pair: beta (3), n x d (6), its norm (3), sqrt (1),
-#   u, v (2), range tests (3), fixed-point split (6), weights (5),
-#   address (2), four shared-memory int32 atomics (4), count (1)    -> 36
+#   per contributing pair: beta (3), alpha^2 = |d|^2 - beta^2 (1), sqrt (1),
+#   u, v (2), support tests (3), fixed-point quantise and split (6),
+#   weights (5), address (2), four shared-memory int32 atomics (4), count (1)
+#                                                                    -> 28
 OPS_PER_CULLED = 11
-OPS_PER_SUPPORT = 36
+OPS_PER_SUPPORT = 28
 
 
 # --------------------------------------------------------------------------
