@@ -40,6 +40,13 @@ namespace si {
 namespace {
 
 constexpr int kWarps = kThreads / 32;
+// Two ways to run the tile ring, chosen per group shape:
+//  * barrier mode (groups of 8+ images): every warp consumes; after each tile
+//    a block barrier, then thread 0 refills the stage just drained;
+//  * producer mode (groups of <= 4 images, where a tile is only a trip or two
+//    per warp and the barrier would dominate): the last warp only produces,
+//    in order, and the other warps release stages through "empty" mbarriers.
+constexpr int kProdConsumers = kWarps - 1;
 
 struct __align__(16) QueryInfo {
     float4 p;
@@ -57,6 +64,10 @@ struct __align__(16) Header {
     int warp_tmp[kWarps];
     unsigned long long grp_weight;
     unsigned long long grp_pix;
+    uint64_t empty[kStages];  // producer mode: consumer warps release stages
+    int fills[kStages];       // fills issued into each stage (both modes, whole kernel)
+    int pfills[kStages];      // fills issued in producer mode (empty-barrier phases)
+    int abort_flag;
 };
 
 constexpr int kHeaderBytes = (sizeof(Header) + 127) / 128 * 128;
@@ -178,7 +189,7 @@ __device__ __forceinline__ void eval_pair(const PairDist &pd, const float4 X, co
 
 // Consumes one staged tile: every lane pairs its slot's query with its
 // candidates; two candidates per lane per trip.
-template <int WT, int LS, bool PROBE>
+template <int WT, int LS, bool PROBE, int NCONS>
 __device__ __forceinline__ void consume_tile(const float4 *__restrict__ tile, const int len, const int warp,
                                              const int lane, const bool active, const float4 P, const float4 N,
                                              const PairConsts &k, const Shape<WT, LS> sh, int *__restrict__ img_q,
@@ -186,7 +197,7 @@ __device__ __forceinline__ void consume_tile(const float4 *__restrict__ tile, co
     const int l2 = sh.log2S();
     const int cpw = 32 >> l2;      // candidates per warp step
     const int sub = lane >> l2;
-    const int stride = kWarps * cpw;
+    const int stride = NCONS * cpw;
     for (int cb = warp * cpw; cb < len; cb += 2 * stride) {
         const int c0 = cb + sub, c1 = cb + stride + sub;
         const bool l0 = active & (c0 < len), l1 = active & (c1 < len);
@@ -224,9 +235,9 @@ struct SmemView {
 
 // Generates the images of one group (units u of item `it`).  Returns false
 // when a bounded wait gave up (the block then stops).
-template <int WT, int LS, bool PROBE>
+template <int WT, int LS, bool PROBE, bool PMODE>
 __device__ bool process_group(const ItemDesc &it, const int u, const int step, const SmemView &sv,
-                              uint32_t &phase_bits, uint32_t &armed) {
+                              uint32_t &phase_bits) {
     Header &H = *sv.H;
     QueryInfo *Q = sv.Q;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -348,6 +359,82 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
         __syncthreads();
         const int total = block_scan_rows(sv.row_len, sv.row_off, nr, H);
         const int ntiles = (total + kTile - 1) / kTile;
+        if constexpr (PMODE) {
+        volatile int *abort_flag = &H.abort_flag;
+        if (warp == kWarps - 1) {
+            // ---- producer warp: fills every tile in order with a running row cursor,
+            // reusing a stage once all consumer warps have released its last tile
+            if (lane == 0) {
+                int cr = 0, co = 0;
+                for (int t = 0; t < ntiles; ++t) {
+                    const int b = t % kStages;
+                    const int j = H.pfills[b];
+                    if (j > 0) {
+                        const uint32_t par = (uint32_t)(j - 1) & 1u;
+                        bool ok = mbar_try_wait(&H.empty[b], par);
+                        const uint64_t t_start = global_ns();
+                        while (!ok && !*abort_flag && global_ns() - t_start <= kWaitLimitNs)
+                            ok = mbar_try_wait(&H.empty[b], par);
+                        if (!ok) {
+                            atomicOr(&H.abort_flag, 1);
+                            break;
+                        }
+                    }
+                    const int need = min(kTile, total - t * kTile);
+                    float4 *dst = sv.tiles + (size_t)b * kTile * 2;
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&H.bar[b], (uint32_t)need * 32u);
+                    int done = 0;
+                    while (done < need && cr < nr) {
+                        const int avail = sv.row_len[cr] - co;
+                        if (avail <= 0) {
+                            ++cr;
+                            co = 0;
+                            continue;
+                        }
+                        const int take = min(need - done, avail);
+                        bulk_copy_g2s(dst + 2 * done, pn + 2 * (int64_t)(sv.row_start[cr] + co),
+                                      (uint32_t)take * 32u, &H.bar[b]);
+                        done += take;
+                        co += take;
+                    }
+                    H.pfills[b] = j + 1;
+                    H.fills[b] += 1;
+                }
+            }
+            __syncwarp();
+            // keep this warp's view of the full-barrier phases in step with the consumers
+            if (!*abort_flag)
+                for (int t = 0; t < ntiles; ++t) phase_bits ^= 1u << (t % kStages);
+        } else {
+            // ---- consumer warps
+            for (int t = 0; t < ntiles; ++t) {
+                const int b = t % kStages;
+                const uint32_t par = (phase_bits >> b) & 1u;
+                bool ok = mbar_try_wait(&H.bar[b], par);
+                if (!ok) {
+                    const uint64_t t_start = global_ns();
+                    while (!ok && !*abort_flag && global_ns() - t_start <= kWaitLimitNs)
+                        ok = mbar_try_wait(&H.bar[b], par);
+                }
+                if (!__all_sync(0xffffffffu, ok)) {
+                    if (lane == 0) atomicOr(&H.abort_flag, 1);
+                    break;
+                }
+                phase_bits ^= 1u << b;
+                const int len = min(kTile, total - t * kTile);
+                if (PROBE && tid < nq) sv.pc_examined[tid] += len;
+                consume_tile<WT, LS, PROBE, kProdConsumers>(sv.tiles + (size_t)b * kTile * 2, len, warp, lane,
+                                                            active, qP, qN, k, sh, img_q, cnt, sv.pc_culled + slot,
+                                                            sv.pc_support + slot, sv.pc_hash + slot);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&H.empty[b]);
+            }
+        }
+        __syncthreads();
+        if (*abort_flag) ok_all = false;
+        __syncthreads();
+        } else {
         // ---- producer state (thread 0): row cursor
         int cr = 0, co = 0;
         auto fill = [&](int t) {
@@ -370,7 +457,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
                 done += take;
                 co += take;
             }
-            armed |= 1u << b;
+            H.fills[b] += 1;
         };
         if (tid == 0) {
             for (int t = 0; t < kStages && t < ntiles; ++t) fill(t);
@@ -380,12 +467,11 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
             const bool ok = mbar_wait_bounded(&H.bar[b], (phase_bits >> b) & 1u, kWaitLimitNs);
             if (ok) {
                 phase_bits ^= 1u << b;
-                if (tid == 0) armed &= ~(1u << b);
                 const int len = min(kTile, total - t * kTile);
                 if (PROBE && tid < nq) sv.pc_examined[tid] += len;
-                consume_tile<WT, LS, PROBE>(sv.tiles + (size_t)b * kTile * 2, len, warp, lane, active, qP, qN, k,
-                                            sh, img_q, cnt, sv.pc_culled + slot, sv.pc_support + slot,
-                                            sv.pc_hash + slot);
+                consume_tile<WT, LS, PROBE, kWarps>(sv.tiles + (size_t)b * kTile * 2, len, warp, lane, active, qP,
+                                                    qN, k, sh, img_q, cnt, sv.pc_culled + slot, sv.pc_support + slot,
+                                                    sv.pc_hash + slot);
             }
             if (__syncthreads_or(!ok)) {
                 ok_all = false;
@@ -393,13 +479,14 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
             }
             if (tid == 0 && t + kStages < ntiles) fill(t + kStages);
         }
+        }
     }
     if (!ok_all) {
         if (tid == 0) {
             atomicOr(it.flags, kFlagTimeout);
             // drain this block's copies still in flight before leaving
             for (int b = 0; b < kStages; ++b)
-                if (armed & (1u << b)) mbar_wait_bounded(&H.bar[b], (phase_bits >> b) & 1u, kWaitLimitNs);
+                if (H.fills[b] > 0) mbar_wait_bounded(&H.bar[b], (uint32_t)(H.fills[b] - 1) & 1u, kWaitLimitNs);
         }
         return false;
     }
@@ -466,7 +553,13 @@ __global__ void __launch_bounds__(kThreads, SI_MIN_BLOCKS) spin_kernel(LaunchArg
     const int tid = threadIdx.x;
 
     if (tid == 0) {
-        for (int b = 0; b < kStages; ++b) mbar_init(&H.bar[b], 1);
+        for (int b = 0; b < kStages; ++b) {
+            mbar_init(&H.bar[b], 1);
+            mbar_init(&H.empty[b], kProdConsumers);
+            H.fills[b] = 0;
+            H.pfills[b] = 0;
+        }
+        H.abort_flag = 0;
         fence_mbar_init();
         H.grp_weight = 0;
         H.grp_pix = 0;
@@ -474,7 +567,6 @@ __global__ void __launch_bounds__(kThreads, SI_MIN_BLOCKS) spin_kernel(LaunchArg
     __syncthreads();
 
     uint32_t phase_bits = 0;  // expected parity per stage (every thread tracks it)
-    uint32_t armed = 0;       // stages with a fill in flight (thread 0)
     bool alive = true;
     int claim_iter = 0;
 
@@ -501,22 +593,23 @@ __global__ void __launch_bounds__(kThreads, SI_MIN_BLOCKS) spin_kernel(LaunchArg
                 // specialised shapes for the common widths, a runtime one otherwise
                 switch (key) {
                     case 16 * 8 + 5:
-                        alive = process_group<16, 5, PROBE>(it, u, step, sv, phase_bits, armed);
+                        alive = process_group<16, 5, PROBE, false>(it, u, step, sv, phase_bits);
                         break;
                     case 32 * 8 + 4:
-                        alive = process_group<32, 4, PROBE>(it, u, step, sv, phase_bits, armed);
+                        alive = process_group<32, 4, PROBE, false>(it, u, step, sv, phase_bits);
                         break;
                     case 32 * 8 + 3:
-                        alive = process_group<32, 3, PROBE>(it, u, step, sv, phase_bits, armed);
+                        alive = process_group<32, 3, PROBE, false>(it, u, step, sv, phase_bits);
                         break;
                     case 64 * 8 + 1:
-                        alive = process_group<64, 1, PROBE>(it, u, step, sv, phase_bits, armed);
+                        alive = process_group<64, 1, PROBE, true>(it, u, step, sv, phase_bits);
                         break;
                     case 64 * 8 + 2:
-                        alive = process_group<64, 2, PROBE>(it, u, step, sv, phase_bits, armed);
+                        alive = process_group<64, 2, PROBE, true>(it, u, step, sv, phase_bits);
                         break;
                     default:
-                        alive = process_group<0, 0, PROBE>(it, u, step, sv, phase_bits, armed);
+                        alive = it.log2S <= 2 ? process_group<0, 0, PROBE, true>(it, u, step, sv, phase_bits)
+                                              : process_group<0, 0, PROBE, false>(it, u, step, sv, phase_bits);
                         break;
                 }
             }
@@ -578,9 +671,16 @@ int choose_log2_group(int W, int requested_group) {
         return l;
     }
     const size_t budget = (size_t)SI_SMEM_BUDGET_KB * 1024;
-    for (int l = 5; l > 0; --l)
-        if (spin_smem_bytes(image_words(W, l)) <= budget) return l;
-    return 0;
+    int l = 0;
+    for (int c = 5; c > 0; --c)
+        if (spin_smem_bytes(image_words(W, c)) <= budget) {
+            l = c;
+            break;
+        }
+    // wide images: when three blocks per SM leave at most two images per
+    // group, four images at two blocks per SM feed each tile better
+    if (l <= 1 && spin_smem_bytes(image_words(W, l + 1)) <= (size_t)113 * 1024) ++l;
+    return l;
 }
 
 }  // namespace si
