@@ -3,7 +3,7 @@
  *
  * Spin images (Sec. 2.1, Algorithm 1): for every query oriented point P with
  * unit normal n and every oriented point X of the set (X = P included),
- *   beta  = n . (X - P),   alpha = |n x (X - P)|  (= sqrt(|X-P|^2 - beta^2)),
+ *   beta  = n . (X - P),   alpha = sqrt(|X-P|^2 - beta^2),
  *   u = W/2 - beta/B (row, from the top),  v = alpha/B (column),
  * X contributes when n . n_X >= cos S (the support-angle test of Algorithm 1)
  * and all four bilinear corners lie inside the W x W image:
@@ -82,6 +82,10 @@ typedef struct si_schedule {
     int32_t num_workers; /* persistent thread blocks P (0 -> all SMs x blocks per SM) */
     int32_t group;       /* images per group: 1, 2, 4, 8, 16 or 32 (0 -> by W) */
     int32_t grid_div;    /* grid cells per candidate radius, 1..16 (0 -> 8) */
+    int32_t slices;      /* blocks that share one group's candidate stream, 1..64; each adds
+                            its partial images into `out` with integer atomics (results are
+                            unchanged).  0 -> auto: 1 when the call has enough groups to fill
+                            the GPU, more for calls with few groups (small requests). */
 } si_schedule;
 
 /* Optional per-image probes (device buffers of m entries, each may be NULL).
@@ -101,7 +105,7 @@ typedef struct si_stats {
     int64_t images;         /* images enqueued on this mesh */
     int32_t overflow;       /* 1 if some pixel of some image exceeded INT32_MAX */
     int32_t timeout;        /* 1 if a bounded device wait gave up (images incomplete) */
-    int32_t bad_query;      /* 1 if a query index was outside [0, n) (that image is not written) */
+    int32_t bad_query;      /* 1 if a query index was outside [0, n) (that image is not computed) */
     int32_t reserved;
     int64_t grid_cells;     /* cells of the most recently built grid */
     int64_t kernel_launches;/* timed spin-kernel launches (see si_set_timing) */
@@ -149,7 +153,7 @@ si_status si_mesh_prepare(si_mesh_t mesh, int32_t W, float bin_size,
  *   cos_support_angle : cos S in [-1, 1]; S >= pi is -1 (no angle test).
  *   out       : device int32[m][W][W].
  * A query index outside [0, n) is detected on the device: its image is not
- * written and si_get_stats reports SI_ERR_INVALID (bad_query). */
+ * computed (its contents are unspecified) and si_get_stats reports SI_ERR_INVALID (bad_query). */
 si_status si_generate(si_mesh_t mesh, const int32_t *query_idx, int64_t m, int32_t W,
                       float bin_size, float cos_support_angle, si_schedule schedule,
                       int32_t *out, si_stream stream);

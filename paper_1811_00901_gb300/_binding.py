@@ -27,7 +27,7 @@ class SpinError(RuntimeError):
 
 class si_schedule(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("min_chunk", ctypes.c_int32), ("num_workers", ctypes.c_int32),
-                ("group", ctypes.c_int32), ("grid_div", ctypes.c_int32)]
+                ("group", ctypes.c_int32), ("grid_div", ctypes.c_int32), ("slices", ctypes.c_int32)]
 
 
 class si_probe(ctypes.Structure):
@@ -138,10 +138,10 @@ def _ptr(t):
     return t.data_ptr()
 
 
-def make_schedule(kind="GSS", min_chunk=1, num_workers=0, group=0, grid_div=0):
+def make_schedule(kind="GSS", min_chunk=1, num_workers=0, group=0, grid_div=0, slices=0):
     if isinstance(kind, str):
         kind = SCHED_NAMES[kind.upper()]
-    return si_schedule(int(kind), int(min_chunk), int(num_workers), int(group), int(grid_div))
+    return si_schedule(int(kind), int(min_chunk), int(num_workers), int(group), int(grid_div), int(slices))
 
 
 # ----------------------------------------------------------------------------

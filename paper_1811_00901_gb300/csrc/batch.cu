@@ -63,6 +63,34 @@ __global__ void qsort_count_kernel(const SortItem *__restrict__ items, const int
     }
 }
 
+// Exact overflow check of sliced items after the spin kernel: an image's
+// pixels (int32 read as signed) sum to 65536 x its contributing pairs unless
+// a pixel wrapped.  One warp per image.
+__global__ void split_check_kernel(const ItemDesc *__restrict__ items, const int64_t *__restrict__ base,
+                                   const int *__restrict__ which, int nsplit, int64_t total) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; g < total; g += warps) {
+        int lo = 0, hi = nsplit - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (base[mid] <= g)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const ItemDesc &it = items[which[lo]];
+        const int64_t q = g - base[lo];
+        const int npix = it.W * it.W;
+        const int32_t *img = it.out + q * npix;
+        long long s = 0;
+        for (int p = lane; p < npix; p += 32) s += img[p];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+        if (lane == 0 && s != 65536ll * it.counts[q]) atomicOr(it.flags, kFlagOverflow);
+    }
+}
+
 // hist holds exclusive offsets on entry and is consumed as a cursor.
 __global__ void qsort_scatter_kernel(const SortItem *__restrict__ items, const int64_t *__restrict__ qbase,
                                      int nitems, int64_t total, int *__restrict__ hist, int *__restrict__ perm) {
@@ -96,13 +124,19 @@ struct Plan {
     std::vector<int64_t> sqbase;
     std::vector<int> sort_of;
     int64_t qtot = 0, htot = 0;
-    size_t o_ctr = 0, o_items = 0, o_pieces = 0, o_steps = 0, o_sitems = 0, o_sqbase = 0, o_hist = 0, o_perm = 0,
-           total_bytes = 0;
+    // sliced items: their index, first image in the concatenated check space,
+    // and the offset of their pair counts
+    std::vector<int> slices;
+    std::vector<int> split_items;
+    std::vector<int64_t> split_base, counts_off;
+    int64_t split_images = 0;
+    size_t o_ctr = 0, o_items = 0, o_pieces = 0, o_steps = 0, o_sitems = 0, o_sqbase = 0, o_split = 0,
+           o_split_items = 0, o_hist = 0, o_perm = 0, o_counts = 0, total_bytes = 0;
     bool empty = false;
 };
 
 si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<si_schedule> &scheds,
-                     int forced_workers, cudaStream_t stream, Plan *p) {
+                     int forced_workers, bool probe, cudaStream_t stream, Plan *p) {
     int dev = 0;
     SI_CUDA(cudaGetDevice(&dev));
     const int nitems = (int)items.size();
@@ -148,6 +182,33 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
         for (int k = 0; k < nitems; ++k) workers = std::max(workers, scheds[k].num_workers);
     if (!workers) workers = num_sms(dev) * per_sm;
     p->workers = workers;
+
+    // ---- candidate slices: a call with few groups would leave most workers
+    // idle (a group is one block's work), so each group's candidate stream is
+    // split over several blocks; probes need whole groups
+    p->slices.assign(nitems, 1);
+    const int auto_k = total_units >= 2 * (int64_t)workers
+                           ? 1
+                           : (int)std::min<int64_t>(64, (2 * (int64_t)workers + total_units - 1) / total_units);
+    total_units = 0;
+    for (int k = 0; k < nitems; ++k) {
+        int K = scheds[k].slices > 0 ? std::min(scheds[k].slices, 64) : auto_k;
+        if (probe) K = 1;
+        p->slices[k] = K;
+        p->units[k] *= K;
+        total_units += p->units[k];
+        if (K > 1 && items[k].m > 0) {
+            p->split_items.push_back(k);
+            p->split_base.push_back(p->split_images);
+            p->counts_off.push_back(p->split_images);
+            p->split_images += items[k].m;
+        }
+    }
+    if (total_units > INT32_MAX) {
+        set_error("too many image groups in one call");
+        return SI_ERR_INVALID;
+    }
+    p->split_base.push_back(p->split_images);
 
     // ---- the scheduled loop: steps made of pieces
     for (int k = 0; k < nitems; ++k)
@@ -229,9 +290,12 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
     p->o_steps = align_up(p->o_pieces + sizeof(Piece) * p->pieces.size(), 256);
     p->o_sitems = align_up(p->o_steps + sizeof(int) * p->step_piece.size(), 256);
     p->o_sqbase = align_up(p->o_sitems + sizeof(SortItem) * p->sitems.size(), 256);
-    p->o_hist = align_up(p->o_sqbase + sizeof(int64_t) * p->sqbase.size(), 256);
+    p->o_split = align_up(p->o_sqbase + sizeof(int64_t) * p->sqbase.size(), 256);
+    p->o_split_items = align_up(p->o_split + sizeof(int64_t) * p->split_base.size(), 256);
+    p->o_hist = align_up(p->o_split_items + sizeof(int) * p->split_items.size(), 256);
     p->o_perm = align_up(p->o_hist + sizeof(int) * (p->htot + 1), 256);
-    p->total_bytes = align_up(p->o_perm + sizeof(int) * p->qtot, 256);
+    p->o_counts = align_up(p->o_perm + sizeof(int) * p->qtot, 256);
+    p->total_bytes = align_up(p->o_counts + sizeof(int) * p->split_images, 256);
     return SI_OK;
 }
 
@@ -294,6 +358,9 @@ void fill_blob(const Plan &p, const std::vector<si_batch_item> &items, const std
             d.p_examined = pr->examined;
         }
     }
+    int *d_counts = reinterpret_cast<int *>(scratch + p.o_counts);
+    for (int k = 0; k < p.nitems; ++k) descs[k].slices = p.slices[k];
+    for (size_t s = 0; s < p.split_items.size(); ++s) descs[p.split_items[s]].counts = d_counts + p.counts_off[s];
     char *h = blob->data();
     std::memcpy(h, descs.data(), sizeof(ItemDesc) * p.nitems);
     std::memcpy(h + (p.o_pieces - p.o_items), p.pieces.data(), sizeof(Piece) * p.pieces.size());
@@ -302,14 +369,29 @@ void fill_blob(const Plan &p, const std::vector<si_batch_item> &items, const std
         std::memcpy(h + (p.o_sitems - p.o_items), p.sitems.data(), sizeof(SortItem) * p.sitems.size());
         std::memcpy(h + (p.o_sqbase - p.o_items), p.sqbase.data(), sizeof(int64_t) * p.sqbase.size());
     }
+    if (!p.split_items.empty()) {
+        std::memcpy(h + (p.o_split - p.o_items), p.split_base.data(), sizeof(int64_t) * p.split_base.size());
+        std::memcpy(h + (p.o_split_items - p.o_items), p.split_items.data(), sizeof(int) * p.split_items.size());
+    }
 }
 
 // Device commands of a planned batch on `stream` (also what a graph captures).
 // Returns the number of kernels recorded in *kernels.
-si_status record_batch(const Plan &p, char *scratch, bool probe, cudaStream_t stream, int *kernels) {
+si_status record_batch(const Plan &p, const std::vector<si_batch_item> &items, char *scratch, bool probe,
+                       cudaStream_t stream, int *kernels) {
     int nk = 0;
     cudaError_t e = cudaMemsetAsync(scratch + p.o_ctr, 0, sizeof(LaunchCounters), stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");
+    // sliced items accumulate into zeroed outputs and pair counts
+    for (int k : p.split_items) {
+        const si_batch_item &it = items[k];
+        e = cudaMemsetAsync(it.out, 0, sizeof(int32_t) * (size_t)it.m * it.W * it.W, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(sliced output)");
+    }
+    if (p.split_images > 0) {
+        e = cudaMemsetAsync(scratch + p.o_counts, 0, sizeof(int) * p.split_images, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(pair counts)");
+    }
     if (p.qtot > 0) {
         int *hist = reinterpret_cast<int *>(scratch + p.o_hist);
         int *perm = reinterpret_cast<int *>(scratch + p.o_perm);
@@ -345,6 +427,14 @@ si_status record_batch(const Plan &p, char *scratch, bool probe, cudaStream_t st
     launch_spin_kernel(a, p.all_static ? p.nsteps : p.workers, p.smem, stream);
     ++nk;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "spin kernel launch");
+    if (p.split_images > 0) {
+        const int blocks = (int)std::min<int64_t>((p.split_images + 7) / 8, 152 * 8);
+        split_check_kernel<<<blocks, 256, 0, stream>>>(
+            a.items, reinterpret_cast<const int64_t *>(scratch + p.o_split),
+            reinterpret_cast<const int *>(scratch + p.o_split_items), (int)p.split_items.size(), p.split_images);
+        ++nk;
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "overflow check launch");
+    }
     *kernels = nk;
     return SI_OK;
 }
@@ -425,22 +515,22 @@ std::vector<char> batch_key(const std::vector<si_batch_item> &items, const std::
 
 si_status enqueue_batch(const std::vector<si_batch_item> &items, const std::vector<si_schedule> &scheds,
                         const std::vector<const si_probe *> &probes, cudaStream_t stream, int forced_workers) {
+    bool probe = false;
+    for (auto *pr : probes)
+        if (pr) probe = true;
     Plan p;
-    si_status st = plan_batch(items, scheds, forced_workers, stream, &p);
+    si_status st = plan_batch(items, scheds, forced_workers, probe, stream, &p);
     if (st != SI_OK || p.empty) return st;
     char *scratch = nullptr;
     st = dev_alloc((void **)&scratch, p.total_bytes, stream);
     if (st != SI_OK) return st;
     std::vector<char> blob;
-    bool probe = false;
-    for (auto *pr : probes)
-        if (pr) probe = true;
     fill_blob(p, items, probes, scratch, &blob);
     st = stage_upload(scratch + p.o_items, blob.data(), blob.size(), stream);
     if (st == SI_OK) {
         TimedRegion tr(reinterpret_cast<Mesh *>(items[0].mesh), stream);
         int nk = 0;
-        st = record_batch(p, scratch, probe, stream, &nk);
+        st = record_batch(p, items, scratch, probe, stream, &nk);
         tr.end(stream);
         note_launches(nk);
         if (st == SI_OK) note_calls(items);
@@ -475,7 +565,7 @@ si_status enqueue_batch_graph(const std::vector<si_batch_item> &items, const std
         }
     }
     Plan p;
-    si_status st = plan_batch(items, scheds, forced_workers, stream, &p);
+    si_status st = plan_batch(items, scheds, forced_workers, false, stream, &p);
     if (st != SI_OK || p.empty) return st;
     GraphEntry e;
     e.key = key;
@@ -493,7 +583,7 @@ si_status enqueue_batch_graph(const std::vector<si_batch_item> &items, const std
         if (err != cudaSuccess) st = cuda_fail(err, "cudaStreamBeginCapture");
     }
     if (st == SI_OK) {
-        st = record_batch(p, e.scratch, false, stream, &e.kernels);
+        st = record_batch(p, items, e.scratch, false, stream, &e.kernels);
         err = cudaStreamEndCapture(stream, &graph);
         if (err != cudaSuccess && st == SI_OK) st = cuda_fail(err, "cudaStreamEndCapture");
     }

@@ -114,6 +114,10 @@ struct ItemDesc {
     int32_t *p_worker;
     int32_t *p_step;
     int64_t *p_examined;
+    // candidate slices per group (>= 1); with more than one, slices add
+    // partial images into a zeroed `out` and per-image pair counts into `counts`
+    int slices;
+    int *counts;  // [m], zeroed, when slices > 1
 };
 
 // A piece of the scheduled loop: units [u0, u1) of item `item`.

@@ -68,6 +68,7 @@ struct __align__(16) Header {
     int fills[kStages];       // fills issued into each stage (both modes, whole kernel)
     int pfills[kStages];      // fills issued in producer mode (empty-barrier phases)
     int abort_flag;
+    int slot_cnt[32];         // sliced groups: contributing pairs per image of this slice
 };
 
 constexpr int kHeaderBytes = (sizeof(Header) + 127) / 128 * 128;
@@ -233,8 +234,24 @@ struct SmemView {
     int *img;
 };
 
-// Generates the images of one group (units u of item `it`).  Returns false
-// when a bounded wait gave up (the block then stops).
+// Row and offset of flat candidate position `first` in a row list with
+// exclusive offsets row_off[0..nr): the last row starting at or before it.
+__device__ __forceinline__ void row_cursor(const int *row_off, int nr, int first, int &cr, int &co) {
+    int lo = 0, hi = nr - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (row_off[mid] <= first)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    cr = lo;
+    co = first - row_off[lo];
+}
+
+// Generates the images of one unit u of item `it` (a group, or one slice of
+// a group's candidate stream).  Returns false when a bounded wait gave up
+// (the block then stops).
 template <int WT, int LS, bool PROBE, bool PMODE>
 __device__ bool process_group(const ItemDesc &it, const int u, const int step, const SmemView &sv,
                               uint32_t &phase_bits) {
@@ -254,8 +271,14 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
     const int slot = lane & (S - 1);
     const int img_words_pad = ((S * W1 * W1) + 3) & ~3;
 
-    const int64_t t0 = (int64_t)u * S;
+    // unit u = slice `sl` of group `g`: with K slices per group, K blocks share
+    // the group's candidate stream and add their partial images into `out`
+    const int K = it.slices > 1 ? it.slices : 1;
+    const int g = K == 1 ? u : u / K;
+    const int sl = K == 1 ? 0 : u - g * K;
+    const int64_t t0 = (int64_t)g * S;
     const int nq = (int)(m - t0 < (int64_t)S ? m - t0 : (int64_t)S);
+    if (K > 1 && tid < 32) H.slot_cnt[tid] = 0;
     // ---- queries of the group
     if (tid < S) {
         if (tid < nq) {
@@ -359,6 +382,9 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
         __syncthreads();
         const int total = block_scan_rows(sv.row_len, sv.row_off, nr, H);
         const int ntiles = (total + kTile - 1) / kTile;
+        // this unit's share of the tiles: [tlo, tlo + nt)
+        const int tlo = (int)((int64_t)ntiles * sl / K);
+        const int nt = (int)((int64_t)ntiles * (sl + 1) / K) - tlo;
         if constexpr (PMODE) {
         volatile int *abort_flag = &H.abort_flag;
         if (warp == kWarps - 1) {
@@ -366,8 +392,10 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
             // reusing a stage once all consumer warps have released its last tile
             if (lane == 0) {
                 int cr = 0, co = 0;
-                for (int t = 0; t < ntiles; ++t) {
-                    const int b = t % kStages;
+                if (nt > 0) row_cursor(sv.row_off, nr, tlo * kTile, cr, co);
+                for (int tt = 0; tt < nt; ++tt) {
+                    const int b = tt % kStages;
+                    const int t = tlo + tt;
                     const int j = H.pfills[b];
                     if (j > 0) {
                         const uint32_t par = (uint32_t)(j - 1) & 1u;
@@ -405,11 +433,12 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
             __syncwarp();
             // keep this warp's view of the full-barrier phases in step with the consumers
             if (!*abort_flag)
-                for (int t = 0; t < ntiles; ++t) phase_bits ^= 1u << (t % kStages);
+                for (int tt = 0; tt < nt; ++tt) phase_bits ^= 1u << (tt % kStages);
         } else {
             // ---- consumer warps
-            for (int t = 0; t < ntiles; ++t) {
-                const int b = t % kStages;
+            for (int tt = 0; tt < nt; ++tt) {
+                const int b = tt % kStages;
+                const int t = tlo + tt;
                 const uint32_t par = (phase_bits >> b) & 1u;
                 bool ok = mbar_try_wait(&H.bar[b], par);
                 if (!ok) {
@@ -437,8 +466,10 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
         } else {
         // ---- producer state (thread 0): row cursor
         int cr = 0, co = 0;
-        auto fill = [&](int t) {
-            const int b = t % kStages;
+        if (tid == 0 && nt > 0) row_cursor(sv.row_off, nr, tlo * kTile, cr, co);
+        auto fill = [&](int tt) {
+            const int b = tt % kStages;
+            const int t = tlo + tt;
             const int need = min(kTile, total - t * kTile);
             float4 *dst = sv.tiles + (size_t)b * kTile * 2;
             fence_proxy_async_smem();
@@ -460,14 +491,14 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
             H.fills[b] += 1;
         };
         if (tid == 0) {
-            for (int t = 0; t < kStages && t < ntiles; ++t) fill(t);
+            for (int tt = 0; tt < kStages && tt < nt; ++tt) fill(tt);
         }
-        for (int t = 0; t < ntiles; ++t) {
-            const int b = t % kStages;
+        for (int tt = 0; tt < nt; ++tt) {
+            const int b = tt % kStages;
             const bool ok = mbar_wait_bounded(&H.bar[b], (phase_bits >> b) & 1u, kWaitLimitNs);
             if (ok) {
                 phase_bits ^= 1u << b;
-                const int len = min(kTile, total - t * kTile);
+                const int len = min(kTile, total - (tlo + tt) * kTile);
                 if (PROBE && tid < nq) sv.pc_examined[tid] += len;
                 consume_tile<WT, LS, PROBE, kWarps>(sv.tiles + (size_t)b * kTile * 2, len, warp, lane, active, qP,
                                                     qN, k, sh, img_q, cnt, sv.pc_culled + slot, sv.pc_support + slot,
@@ -477,7 +508,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
                 ok_all = false;
                 break;
             }
-            if (tid == 0 && t + kStages < ntiles) fill(t + kStages);
+            if (tid == 0 && tt + kStages < nt) fill(tt + kStages);
         }
         }
     }
@@ -502,8 +533,20 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
         const int i = p / W, j = p - i * W;
         const int v = sv.img[(i * W1 + j) * S + q];
         const int qs = Q[q].slot;
-        if (qs >= 0) __stcs(out + (int64_t)qs * npix + p, v);
+        if (qs >= 0) {
+            if (K == 1)
+                __stcs(out + (int64_t)qs * npix + p, v);
+            else if (v != 0)
+                atomicAdd(out + (int64_t)qs * npix + p, v);  // partial image of one slice
+        }
         pix += v;
+    }
+    if (K > 1) {
+        // contributing pairs per image, summed over slices for the exact
+        // overflow check that runs after the kernel
+        if (active && cnt) atomicAdd(&H.slot_cnt[slot], cnt);
+        __syncthreads();
+        if (tid < nq && Q[tid].slot >= 0 && H.slot_cnt[tid]) atomicAdd(&it.counts[Q[tid].slot], H.slot_cnt[tid]);
     }
     // ---- exact overflow check of the group: the written pixels (int32 read
     // as signed) sum to 65536 x pairs unless a pixel wrapped
