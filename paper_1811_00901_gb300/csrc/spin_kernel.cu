@@ -69,6 +69,7 @@ struct __align__(16) Header {
     int pfills[kStages];      // fills issued in producer mode (empty-barrier phases)
     int abort_flag;
     int slot_cnt[32];         // sliced groups: contributing pairs per image of this slice
+    int cur_r, cur_o;          // barrier mode: producer row cursor
 };
 
 constexpr int kHeaderBytes = (sizeof(Header) + 127) / 128 * 128;
@@ -349,8 +350,6 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
     const bool active = slot < nq;
     int cnt = 0;
     int *img_q = sv.img + slot;
-    const float gmin0 = H.gmin[0], gmin1 = H.gmin[1], gmin2 = H.gmin[2];
-    const float gmax0 = H.gmax[0], gmax1 = H.gmax[1], gmax2 = H.gmax[2];
     const int ylo = H.ylo, zlo = H.zlo;
     const int ny = H.yhi - ylo + 1, nz = H.zhi - zlo + 1;
     const int nrows_total = ny * nz;
@@ -364,14 +363,14 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
             const int y = ylo + rr % ny, z = zlo + rr / ny;
             const float sy0 = fmaf((float)y, cell, oy), sy1 = sy0 + cell;
             const float sz0 = fmaf((float)z, cell, oz), sz1 = sz0 + cell;
-            const float gy = fmaxf(0.0f, fmaxf(sy0 - gmax1, gmin1 - sy1) - margin);
-            const float gz = fmaxf(0.0f, fmaxf(sz0 - gmax2, gmin2 - sz1) - margin);
+            const float gy = fmaxf(0.0f, fmaxf(sy0 - H.gmax[1], H.gmin[1] - sy1) - margin);
+            const float gz = fmaxf(0.0f, fmaxf(sz0 - H.gmax[2], H.gmin[2] - sz1) - margin);
             const float rem = k.Rc2 - gy * gy - gz * gz;
             int start = 0, len = 0;
             if (rem >= 0.0f) {
                 const float rx = sqrtf(rem) + margin;
-                const int x0 = cell_coord(gmin0 - rx, ox, inv, dx_);
-                const int x1 = cell_coord(gmax0 + rx, ox, inv, dx_);
+                const int x0 = cell_coord(H.gmin[0] - rx, ox, inv, dx_);
+                const int x1 = cell_coord(H.gmax[0] + rx, ox, inv, dx_);
                 const int c0 = (z * dy_ + y) * dx_ + x0;
                 start = cstart[c0];
                 len = cstart[c0 + (x1 - x0) + 1] - start;
@@ -465,9 +464,14 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
         __syncthreads();
         } else {
         // ---- producer state (thread 0): row cursor
-        int cr = 0, co = 0;
-        if (tid == 0 && nt > 0) row_cursor(sv.row_off, nr, tlo * kTile, cr, co);
+        if (tid == 0) {
+            int cr0 = 0, co0 = 0;
+            if (nt > 0) row_cursor(sv.row_off, nr, tlo * kTile, cr0, co0);
+            H.cur_r = cr0;
+            H.cur_o = co0;
+        }
         auto fill = [&](int tt) {
+            int cr = H.cur_r, co = H.cur_o;
             const int b = tt % kStages;
             const int t = tlo + tt;
             const int need = min(kTile, total - t * kTile);
@@ -488,6 +492,8 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
                 done += take;
                 co += take;
             }
+            H.cur_r = cr;
+            H.cur_o = co;
             H.fills[b] += 1;
         };
         if (tid == 0) {
