@@ -143,6 +143,23 @@ def _measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def _quartiles(xs):
+    q = np.percentile(np.asarray(xs, dtype=np.float64), [25, 50, 75])
+    return [float(v) for v in q]
+
+
+def _peak_clocks(peaks, clk):
+    """SM clocks to quote the ALU peak at: the maximum, the median seen during
+    the timed region, and the median under a long power-capped load."""
+    fs = [float(peaks.get("sm_max_mhz", 2070.0))]
+    if clk and clk.get("sm_mhz"):
+        fs.append(float(clk["sm_mhz"]))
+    cul = peaks.get("clocks_under_load") or {}
+    if cul.get("sm_mhz_median"):
+        fs.append(float(cul["sm_mhz_median"]))
+    return sorted(set(fs), reverse=True)
+
+
 def _kernel_source_hash():
     h = hashlib.sha256()
     for name in ("spin_kernel.cu", "device_common.cuh", "internal.h"):
@@ -277,7 +294,9 @@ def run_ours(args):
                          "images_per_s": job_throughput(m, args.steps, world, total_ms),
                          "culled_pairs_per_s": job_throughput(n_culled, args.steps, world, total_ms),
                          "kernel_ms": statistics.median(kms),
-                         "step_ms_p50": statistics.median(times)}
+                         "kernel_ms_quartiles": _quartiles(kms),
+                         "step_ms_quartiles": _quartiles(times),
+                         "setup_ms": statistics.median([t - k for t, k in zip(times, kms)])}
         kernel_ms[name] = statistics.median(kms)
     clk = clocks.stop()
     del launches0
@@ -320,6 +339,9 @@ def run_ours(args):
                 "kernel": "spin_kernel (persistent, %s)" % best, "kernel_ms": k_ms,
                 "peak_source": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)" % (sms, f_mhz, peak_src),
                 "ops_per_culled_pair": OPS_PER_CULLED, "ops_per_support_pair": OPS_PER_SUPPORT,
+                "peak_at_clocks": {"%.0f_mhz" % f: {"peak": sms * 128 * f * 1e6 / 1e12,
+                                                    "frac": achieved / (sms * 128 * f * 1e6)}
+                                   for f in _peak_clocks(peaks, clk)},
                 "write_gbs": m * W * W * 4 / (k_ms / 1e3) / 1e9,
                 "write_frac_of_hbm": (m * W * W * 4 / (k_ms / 1e3) / 1e9) / float(peaks.get("hbm_gbs", 6800.0)),
                 "smem_atomics": {"achieved_per_s": 4 * n_support / (k_ms / 1e3),
@@ -336,7 +358,9 @@ def run_ours(args):
             "support_pairs_per_step": n_support, "examined_pairs_per_step": n_examined,
             "stencil_overhead": n_examined / max(1, n_culled),
             "by_schedule": {k: {"images_per_s": v["images_per_s"], "ms_per_step": v["ms_per_step"],
-                                "kernel_ms": v["kernel_ms"]} for k, v in results.items()},
+                                "kernel_ms": v["kernel_ms"], "kernel_ms_quartiles": v["kernel_ms_quartiles"],
+                                "step_ms_quartiles": v["step_ms_quartiles"],
+                                "mesh_and_grid_ms": v["setup_ms"]} for k, v in results.items()},
             "dls_over_static": r["images_per_s"] / results["STATIC"]["images_per_s"],
             "e2e": e2e, "roofline": roofline,
             "gpu_launches": int(timed_launches), "clocks": clk}
@@ -605,7 +629,7 @@ def main():
     ap.add_argument("--profile-workload", default="heightfield", choices=["heightfield", "sphere", "scene"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=15)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
