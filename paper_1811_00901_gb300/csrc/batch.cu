@@ -116,6 +116,7 @@ struct Plan {
     std::vector<int> log2S, units;
     size_t max_img_words = 4, smem = 0;
     int workers = 0;
+    int modes = 0;  // tile-ring disciplines of the items' group shapes
     bool all_static = true;
     int nsteps = 0;
     std::vector<Piece> pieces;
@@ -172,7 +173,9 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
     }
     p->smem = spin_smem_bytes(p->max_img_words);
     SI_CUDA(setup_spin_kernel_attributes(p->smem));
-    const int per_sm = blocks_per_sm_for(p->smem);
+    p->modes = 0;
+    for (int k = 0; k < nitems; ++k) p->modes |= ring_mode(p->log2S[k]);
+    const int per_sm = blocks_per_sm_for(p->smem, p->modes);
     if (per_sm < 1) {
         set_error("spin kernel does not fit on an SM with %zu bytes of shared memory", p->smem);
         return SI_ERR_INVALID;
@@ -424,6 +427,7 @@ si_status record_batch(const Plan &p, const std::vector<si_batch_item> &items, c
     a.nitems = p.nitems;
     a.img_words = (int)p.max_img_words;
     a.probe = probe ? 1 : 0;
+    a.modes = p.modes;
     launch_spin_kernel(a, p.all_static ? p.nsteps : p.workers, p.smem, stream);
     ++nk;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "spin kernel launch");

@@ -141,7 +141,13 @@ struct LaunchArgs {
     int nitems;
     int img_words;          // shared words reserved for images (max over items)
     int probe;
+    int modes = 0;          // tile-ring disciplines present (kModeBarrier | kModeProducer); 0 = both
 };
+
+// Tile-ring discipline of a group shape: groups of <= 4 images run a producer
+// warp, larger groups a block barrier per tile.
+constexpr int kModeBarrier = 1, kModeProducer = 2;
+inline int ring_mode(int log2S) { return log2S <= 2 ? kModeProducer : kModeBarrier; }
 
 // ---------------------------------------------------------- host helpers --
 // Column support threshold: v = alpha / B < W - 1  <=>  alpha^2 < ((W-1) B)^2.
@@ -155,7 +161,8 @@ float grid_cell_for(const Mesh *m, int W, float bin, int grid_div);
 int choose_log2_group(int W, int requested_group);
 size_t image_words(int W, int log2S);
 size_t spin_smem_bytes(size_t img_words);
-int blocks_per_sm_for(size_t smem_bytes);
+// Resident spin-kernel blocks per SM for the instance that runs `modes`.
+int blocks_per_sm_for(size_t smem_bytes, int modes);
 int num_sms(int device);
 
 // Chunk rules (host side, one implementation for every caller).

@@ -153,11 +153,19 @@ __device__ __forceinline__ PairDist pair_dist(const float4 X, const float4 P) {
 // Evaluates the rest of one (query, candidate) pair and splats it when it
 // contributes.  Every contributing pair has |d|^2 < R^2 < Rc2, so the cull
 // itself is not part of the support decision.
+// fl32(x + 2^23) for 0 <= x < 2^23 has the exponent field of 2^23; its top 16
+// bits read kMagicHi + (rn(x) >> 16).
+constexpr int kMagicHi = 0x4B00;
+
+// Evaluates the rest of one (query, candidate) pair and splats it when it
+// contributes.  Every contributing pair has |d|^2 < R^2 < Rc2, so the cull
+// itself is not part of the support decision.  `img_adj` is the slot's pixel
+// (0, 0) moved back by the exponent bias that the raw coordinate bits carry
+// (kMagicHi rows and kMagicHi columns).
 template <int WT, int LS, bool PROBE>
-__device__ __forceinline__ void eval_pair(const PairDist &pd, const float4 X, const float4 NX, const bool live,
-                                          const float4 N, const PairConsts &k, const Shape<WT, LS> sh,
-                                          int *__restrict__ img_q, int &cnt, int *pc_c, int *pc_s,
-                                          unsigned *pc_h) {
+__device__ __forceinline__ void eval_pair(const PairDist &pd, const float4 NX, const bool live, const float4 N,
+                                          const PairConsts &k, const Shape<WT, LS> sh, int *img_adj, int &cnt,
+                                          int *pc_s) {
     const float dx = pd.dx, dy = pd.dy, dz = pd.dz, d2 = pd.d2;
     const float ca = fmaf(N.z, NX.z, fmaf(N.y, NX.y, N.x * NX.x));
     const float beta = fmaf(N.z, dz, fmaf(N.y, dy, N.x * dx));
@@ -165,22 +173,21 @@ __device__ __forceinline__ void eval_pair(const PairDist &pd, const float4 X, co
     const float u = fmaf(-beta, k.invB, k.halfW);
     const bool in = live & (ca >= k.cosS) & (u >= 0.0f) & (u < k.umax) & (a2 < k.amax2);
     if (PROBE && in) atomicAdd(pc_s, 1);
-    (void)pc_c;
-    (void)pc_h;
-    (void)X;
     // alpha / B through the approximate reciprocal square root; the support
     // decision above does not depend on it, and 16-bit quantisation absorbs
     // its last-bit error
     const float v = a2 * rsqrtf(fmaxf(a2, 1e-30f)) * k.invB;
-    // U = rn(u * 2^16): u * 2^16 is exact, adding 2^23 rounds it to an integer
-    // held in the low 23 mantissa bits (0 <= U < 2^23 since u < W - 1 <= 127)
-    const unsigned U = __float_as_uint(fmaf(u, 65536.0f, 8388608.0f)) & 0x7FFFFFu;
-    const unsigned V = __float_as_uint(fmaf(v, 65536.0f, 8388608.0f)) & 0x7FFFFFu;
-    const unsigned A = U & 0xFFFFu, Bq = V & 0xFFFFu;
-    const unsigned w11 = (A * Bq + 32768u) >> 16;
+    // U = rn(u * 2^16): u * 2^16 is exact and below 2^23 (0 <= u < W - 1 <= 127
+    // for a contributing pair), so adding 2^23 rounds it to an integer held in
+    // the low 23 bits; the low 16 bits are the fraction, the top 16 the row
+    // plus kMagicHi
+    const uint32_t Ub = __float_as_uint(fmaf(u, 65536.0f, 8388608.0f));
+    const uint32_t Vb = __float_as_uint(fmaf(v, 65536.0f, 8388608.0f));
+    const uint32_t A = Ub & 0xFFFFu, Bq = Vb & 0xFFFFu;
+    const uint32_t w11 = (A * Bq + 32768u) >> 16;
     if (in) {
-        const int S = sh.S(), rw = sh.row_words();
-        int *p0 = img_q + ((int)(U >> 16) * rw + ((int)(V >> 16) << sh.log2S()));
+        const int rw = sh.row_words(), S = sh.S();
+        int *p0 = img_adj + ((int)(Ub >> 16) * rw + (int)(Vb >> 16) * S);
         atomicAdd(p0, (int)(65536u - A - Bq + w11));
         atomicAdd(p0 + rw, (int)(A - w11));
         atomicAdd(p0 + S, (int)(Bq - w11));
@@ -189,40 +196,94 @@ __device__ __forceinline__ void eval_pair(const PairDist &pd, const float4 X, co
     }
 }
 
+// One warp trip: two candidates per lane, at p0 and p1 (position, normal).
+template <int WT, int LS, bool PROBE>
+__device__ __forceinline__ void trip(const float4 *p0, const float4 *p1, const bool l0, const bool l1,
+                                     const float4 P, const float4 N, const PairConsts &k, const Shape<WT, LS> sh,
+                                     int *img_adj, int &cnt, int *pc_c, int *pc_s, unsigned *pc_h) {
+    const float4 X0 = p0[0], X1 = p1[0];
+    const PairDist d0 = pair_dist(X0, P), d1 = pair_dist(X1, P);
+    const bool near0 = l0 & (d0.d2 <= k.Rc2), near1 = l1 & (d1.d2 <= k.Rc2);
+    if (PROBE) {
+        if (near0) {
+            atomicAdd(pc_c, 1);
+            atomicAdd(pc_h, fmix32(__float_as_uint(X0.w)));
+        }
+        if (near1) {
+            atomicAdd(pc_c, 1);
+            atomicAdd(pc_h, fmix32(__float_as_uint(X1.w)));
+        }
+    }
+    // warp-uniform skip: no lane's pair survives the distance cull
+    if (!__any_sync(0xffffffffu, near0 | near1)) return;
+    const float4 N0 = p0[1], N1 = p1[1];
+    eval_pair<WT, LS, PROBE>(d0, N0, near0, N, k, sh, img_adj, cnt, pc_s);
+    eval_pair<WT, LS, PROBE>(d1, N1, near1, N, k, sh, img_adj, cnt, pc_s);
+}
+
+// Whether a full tile (kTile candidates) of this shape takes a path without
+// per-lane range checks: compile-time shapes only.
+template <int WT, int LS, int NCONS>
+constexpr bool has_full_path() {
+    return WT > 0 && kTile % (2 * (NCONS == kWarps ? NCONS : 1) * (32 >> LS)) == 0;
+}
+
 // Consumes one staged tile: every lane pairs its slot's query with its
-// candidates; two candidates per lane per trip.
-template <int WT, int LS, bool PROBE, int NCONS>
+// candidates; two candidates per lane per trip.  With FULL the tile holds
+// kTile candidates and every trip is in range:
+//  * all warps consuming (NCONS == kWarps): warp w takes trips at candidate
+//    w*cpw + 2*NCONS*cpw*t (a compile-time count, unrolled);
+//  * NCONS consumer warps: trip t covers candidates [2*cpw*t, 2*cpw*(t+1)),
+//    dealt round-robin.
+template <int WT, int LS, bool PROBE, int NCONS, bool FULL>
 __device__ __forceinline__ void consume_tile(const float4 *__restrict__ tile, const int len, const int warp,
                                              const int lane, const bool active, const float4 P, const float4 N,
-                                             const PairConsts &k, const Shape<WT, LS> sh, int *__restrict__ img_q,
-                                             int &cnt, int *pc_c, int *pc_s, unsigned *pc_h) {
+                                             const PairConsts &k, const Shape<WT, LS> sh, int *img_adj, int &cnt,
+                                             int *pc_c, int *pc_s, unsigned *pc_h) {
     const int l2 = sh.log2S();
     const int cpw = 32 >> l2;      // candidates per warp step
     const int sub = lane >> l2;
     const int stride = NCONS * cpw;
-    for (int cb = warp * cpw; cb < len; cb += 2 * stride) {
-        const int c0 = cb + sub, c1 = cb + stride + sub;
-        const bool l0 = active & (c0 < len), l1 = active & (c1 < len);
-        const int i0 = l0 ? c0 : 0, i1 = l1 ? c1 : 0;
-        const float4 X0 = tile[2 * i0], X1 = tile[2 * i1];
-        const PairDist d0 = pair_dist(X0, P), d1 = pair_dist(X1, P);
-        const bool near0 = l0 & (d0.d2 <= k.Rc2), near1 = l1 & (d1.d2 <= k.Rc2);
-        if (PROBE) {
-            if (near0) {
-                atomicAdd(pc_c, 1);
-                atomicAdd(pc_h, fmix32(__float_as_uint(X0.w)));
-            }
-            if (near1) {
-                atomicAdd(pc_c, 1);
-                atomicAdd(pc_h, fmix32(__float_as_uint(X1.w)));
-            }
+    if constexpr (FULL && NCONS == kWarps) {
+        constexpr int kStride = NCONS * (32 >> LS);
+        constexpr int kTrips = kTile / (2 * kStride);
+        const float4 *t0 = tile + 2 * (warp * cpw + sub);
+#pragma unroll 4
+        for (int tr = 0; tr < kTrips; ++tr)
+            trip<WT, LS, PROBE>(t0 + 4 * tr * kStride, t0 + 4 * tr * kStride + 2 * kStride, active, active, P, N,
+                                k, sh, img_adj, cnt, pc_c, pc_s, pc_h);
+    } else if constexpr (FULL) {
+        constexpr int kCpw = 32 >> LS;
+        constexpr int kTrips = kTile / (2 * kCpw);
+        const float4 *t0 = tile + 2 * sub;
+        for (int tr = warp; tr < kTrips; tr += NCONS)
+            trip<WT, LS, PROBE>(t0 + 4 * tr * kCpw, t0 + 4 * tr * kCpw + 2 * kCpw, active, active, P, N, k, sh,
+                                img_adj, cnt, pc_c, pc_s, pc_h);
+    } else {
+        for (int cb = warp * cpw; cb < len; cb += 2 * stride) {
+            const int c0 = cb + sub, c1 = cb + stride + sub;
+            const bool l0 = active & (c0 < len), l1 = active & (c1 < len);
+            const int i0 = l0 ? c0 : 0, i1 = l1 ? c1 : 0;
+            trip<WT, LS, PROBE>(tile + 2 * i0, tile + 2 * i1, l0, l1, P, N, k, sh, img_adj, cnt, pc_c, pc_s, pc_h);
         }
-        // warp-uniform skip: no lane's pair survives the distance cull
-        if (!__any_sync(0xffffffffu, near0 | near1)) continue;
-        const float4 N0 = tile[2 * i0 + 1], N1 = tile[2 * i1 + 1];
-        eval_pair<WT, LS, PROBE>(d0, X0, N0, near0, N, k, sh, img_q, cnt, pc_c, pc_s, pc_h);
-        eval_pair<WT, LS, PROBE>(d1, X1, N1, near1, N, k, sh, img_q, cnt, pc_c, pc_s, pc_h);
     }
+}
+
+// Consumes a tile, through the range-check-free path when it is full.
+template <int WT, int LS, bool PROBE, int NCONS>
+__device__ __forceinline__ void consume_any(const float4 *__restrict__ tile, const int len, const int warp,
+                                            const int lane, const bool active, const float4 P, const float4 N,
+                                            const PairConsts &k, const Shape<WT, LS> sh, int *img_adj, int &cnt,
+                                            int *pc_c, int *pc_s, unsigned *pc_h) {
+    if constexpr (has_full_path<WT, LS, NCONS>()) {
+        if (len == kTile) {
+            consume_tile<WT, LS, PROBE, NCONS, true>(tile, len, warp, lane, active, P, N, k, sh, img_adj, cnt, pc_c,
+                                                     pc_s, pc_h);
+            return;
+        }
+    }
+    consume_tile<WT, LS, PROBE, NCONS, false>(tile, len, warp, lane, active, P, N, k, sh, img_adj, cnt, pc_c, pc_s,
+                                              pc_h);
 }
 
 struct SmemView {
@@ -349,7 +410,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
     const float4 qN = Q[slot].n;
     const bool active = slot < nq;
     int cnt = 0;
-    int *img_q = sv.img + slot;
+    int *img_adj = sv.img + slot - kMagicHi * (sh.row_words() + S);
     const int ylo = H.ylo, zlo = H.zlo;
     const int ny = H.yhi - ylo + 1, nz = H.zhi - zlo + 1;
     const int nrows_total = ny * nz;
@@ -452,9 +513,9 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
                 phase_bits ^= 1u << b;
                 const int len = min(kTile, total - t * kTile);
                 if (PROBE && tid < nq) sv.pc_examined[tid] += len;
-                consume_tile<WT, LS, PROBE, kProdConsumers>(sv.tiles + (size_t)b * kTile * 2, len, warp, lane,
-                                                            active, qP, qN, k, sh, img_q, cnt, sv.pc_culled + slot,
-                                                            sv.pc_support + slot, sv.pc_hash + slot);
+                consume_any<WT, LS, PROBE, kProdConsumers>(sv.tiles + (size_t)b * kTile * 2, len, warp, lane,
+                                                           active, qP, qN, k, sh, img_adj, cnt, sv.pc_culled + slot,
+                                                           sv.pc_support + slot, sv.pc_hash + slot);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&H.empty[b]);
             }
@@ -506,9 +567,9 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
                 phase_bits ^= 1u << b;
                 const int len = min(kTile, total - (tlo + tt) * kTile);
                 if (PROBE && tid < nq) sv.pc_examined[tid] += len;
-                consume_tile<WT, LS, PROBE, kWarps>(sv.tiles + (size_t)b * kTile * 2, len, warp, lane, active, qP,
-                                                    qN, k, sh, img_q, cnt, sv.pc_culled + slot, sv.pc_support + slot,
-                                                    sv.pc_hash + slot);
+                consume_any<WT, LS, PROBE, kWarps>(sv.tiles + (size_t)b * kTile * 2, len, warp, lane, active, qP,
+                                                   qN, k, sh, img_adj, cnt, sv.pc_culled + slot, sv.pc_support + slot,
+                                                   sv.pc_hash + slot);
             }
             if (__syncthreads_or(!ok)) {
                 ok_all = false;
@@ -583,8 +644,18 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
     return true;
 }
 
-template <bool PROBE>
-__global__ void __launch_bounds__(kThreads, SI_MIN_BLOCKS) spin_kernel(LaunchArgs a) {
+// MODES: the tile-ring disciplines compiled in (kModeBarrier | kModeProducer);
+// a launch whose groups all use one discipline runs the instance without the
+// other, whose registers are then allocated for its own loop alone.  Groups
+// in producer mode hold >= 67 KB of images, so at most two blocks fit on an
+// SM: that instance may use the registers of two blocks.
+template <int MODES>
+constexpr int min_blocks_for() {
+    return MODES == kModeProducer ? 2 : SI_MIN_BLOCKS;
+}
+
+template <bool PROBE, int MODES>
+__global__ void __launch_bounds__(kThreads, min_blocks_for<MODES>()) spin_kernel(LaunchArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     SmemView sv;
     sv.H = reinterpret_cast<Header *>(smem);
@@ -640,26 +711,37 @@ __global__ void __launch_bounds__(kThreads, SI_MIN_BLOCKS) spin_kernel(LaunchArg
             const int key = it.W * 8 + it.log2S;
             for (int u = pc.u0; u < pc.u1 && alive; ++u) {
                 // specialised shapes for the common widths, a runtime one otherwise
-                switch (key) {
-                    case 16 * 8 + 5:
-                        alive = process_group<16, 5, PROBE, false>(it, u, step, sv, phase_bits);
-                        break;
-                    case 32 * 8 + 4:
-                        alive = process_group<32, 4, PROBE, false>(it, u, step, sv, phase_bits);
-                        break;
-                    case 32 * 8 + 3:
-                        alive = process_group<32, 3, PROBE, false>(it, u, step, sv, phase_bits);
-                        break;
-                    case 64 * 8 + 1:
-                        alive = process_group<64, 1, PROBE, true>(it, u, step, sv, phase_bits);
-                        break;
-                    case 64 * 8 + 2:
-                        alive = process_group<64, 2, PROBE, true>(it, u, step, sv, phase_bits);
-                        break;
-                    default:
-                        alive = it.log2S <= 2 ? process_group<0, 0, PROBE, true>(it, u, step, sv, phase_bits)
-                                              : process_group<0, 0, PROBE, false>(it, u, step, sv, phase_bits);
-                        break;
+                if (it.log2S <= 2) {
+                    if constexpr ((MODES & kModeProducer) != 0) {
+                        switch (key) {
+                            case 64 * 8 + 1:
+                                alive = process_group<64, 1, PROBE, true>(it, u, step, sv, phase_bits);
+                                break;
+                            case 64 * 8 + 2:
+                                alive = process_group<64, 2, PROBE, true>(it, u, step, sv, phase_bits);
+                                break;
+                            default:
+                                alive = process_group<0, 0, PROBE, true>(it, u, step, sv, phase_bits);
+                                break;
+                        }
+                    }
+                } else {
+                    if constexpr ((MODES & kModeBarrier) != 0) {
+                        switch (key) {
+                            case 16 * 8 + 5:
+                                alive = process_group<16, 5, PROBE, false>(it, u, step, sv, phase_bits);
+                                break;
+                            case 32 * 8 + 4:
+                                alive = process_group<32, 4, PROBE, false>(it, u, step, sv, phase_bits);
+                                break;
+                            case 32 * 8 + 3:
+                                alive = process_group<32, 3, PROBE, false>(it, u, step, sv, phase_bits);
+                                break;
+                            default:
+                                alive = process_group<0, 0, PROBE, false>(it, u, step, sv, phase_bits);
+                                break;
+                        }
+                    }
                 }
             }
         }
@@ -688,27 +770,40 @@ size_t spin_smem_bytes(size_t img_words) { return (size_t)off_images() + img_wor
 cudaError_t setup_spin_kernel_attributes(size_t smem_bytes) {
     static size_t done = 0;
     if (smem_bytes <= done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(spin_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(spin_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    const int bytes = (int)smem_bytes;
+    const cudaFuncAttribute attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(spin_kernel<false, kModeBarrier | kModeProducer>, attr, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(spin_kernel<false, kModeBarrier>, attr, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(spin_kernel<false, kModeProducer>, attr, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(spin_kernel<true, kModeBarrier | kModeProducer>, attr, bytes);
     if (e == cudaSuccess) done = smem_bytes;
     return e;
 }
 
-int blocks_per_sm_for(size_t smem_bytes) {
+int blocks_per_sm_for(size_t smem_bytes, int modes) {
     int n = 0;
     if (setup_spin_kernel_attributes(smem_bytes) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spin_kernel<false>, kThreads, smem_bytes) != cudaSuccess)
-        return 0;
-    return n;
+    cudaError_t e;
+    if (modes == kModeBarrier)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spin_kernel<false, kModeBarrier>, kThreads, smem_bytes);
+    else if (modes == kModeProducer)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spin_kernel<false, kModeProducer>, kThreads,
+                                                          smem_bytes);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spin_kernel<false, kModeBarrier | kModeProducer>,
+                                                          kThreads, smem_bytes);
+    return e == cudaSuccess ? n : 0;
 }
 
 void launch_spin_kernel(const LaunchArgs &a, int blocks, size_t smem, cudaStream_t stream) {
     if (a.probe)
-        spin_kernel<true><<<blocks, kThreads, smem, stream>>>(a);
+        spin_kernel<true, kModeBarrier | kModeProducer><<<blocks, kThreads, smem, stream>>>(a);
+    else if (a.modes == kModeBarrier)
+        spin_kernel<false, kModeBarrier><<<blocks, kThreads, smem, stream>>>(a);
+    else if (a.modes == kModeProducer)
+        spin_kernel<false, kModeProducer><<<blocks, kThreads, smem, stream>>>(a);
     else
-        spin_kernel<false><<<blocks, kThreads, smem, stream>>>(a);
+        spin_kernel<false, kModeBarrier | kModeProducer><<<blocks, kThreads, smem, stream>>>(a);
 }
 
 // Largest group (power of two, <= 32, or the requested one) whose images fit
