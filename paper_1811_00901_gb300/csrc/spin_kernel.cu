@@ -21,8 +21,8 @@
 //     shared memory (pixel p of slot q at word p*S + q): the 32 lanes of a
 //     warp hit at most 32/S words per bank, whatever pixels they splat.
 //   * Each lane evaluates two candidates per loop trip without branches (the
-//     two chains interleave); a warp skips the trip when no lane's pair
-//     survives the distance cull.
+//     two chains interleave); only the splat of a contributing pair is
+//     behind a branch.  Full tiles take a loop without per-lane range checks.
 //
 // Per pair (P = query, X = candidate, FP32, differences taken directly):
 //   d = X - P; cull if fl32(|d|^2) > Rc2; angle test n.n_X >= cos S;
@@ -214,8 +214,6 @@ __device__ __forceinline__ void trip(const float4 *p0, const float4 *p1, const b
             atomicAdd(pc_h, fmix32(__float_as_uint(X1.w)));
         }
     }
-    // warp-uniform skip: no lane's pair survives the distance cull
-    if (!__any_sync(0xffffffffu, near0 | near1)) return;
     const float4 N0 = p0[1], N1 = p1[1];
     eval_pair<WT, LS, PROBE>(d0, N0, near0, N, k, sh, img_adj, cnt, pc_s);
     eval_pair<WT, LS, PROBE>(d1, N1, near1, N, k, sh, img_adj, cnt, pc_s);
