@@ -171,10 +171,11 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
         set_error("too many image groups in one call");
         return SI_ERR_INVALID;
     }
-    p->smem = spin_smem_bytes(p->max_img_words);
-    SI_CUDA(setup_spin_kernel_attributes(p->smem));
     p->modes = 0;
     for (int k = 0; k < nitems; ++k) p->modes |= ring_mode(p->log2S[k]);
+    p->modes = launch_modes(p->modes, probe);
+    p->smem = spin_smem_bytes(p->max_img_words, p->modes);
+    SI_CUDA(setup_spin_kernel_attributes(p->smem));
     const int per_sm = blocks_per_sm_for(p->smem, p->modes);
     if (per_sm < 1) {
         set_error("spin kernel does not fit on an SM with %zu bytes of shared memory", p->smem);

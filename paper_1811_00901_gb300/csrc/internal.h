@@ -35,13 +35,21 @@ si_status cuda_fail(cudaError_t e, const char *what);
 #define SI_SMEM_BUDGET_KB 75
 #endif
 constexpr int kThreads = SI_THREADS;  // threads per spin-kernel block
-#ifndef SI_TILE
-#define SI_TILE 256
+#ifndef SI_TILE_BARRIER
+#define SI_TILE_BARRIER 448
+#endif
+#ifndef SI_TILE_PRODUCER
+#define SI_TILE_PRODUCER 512
 #endif
 #ifndef SI_STAGES
-#define SI_STAGES 3
+#define SI_STAGES 2
 #endif
-constexpr int kTile = SI_TILE;      // candidate points per staged tile (32 B each)
+// Candidate points per staged tile (32 B each), per tile-ring discipline: the
+// larger the tile, the fewer block barriers or stage hand-offs per candidate;
+// the barrier ring is bounded by three blocks per SM, the producer ring by two.
+constexpr int kTileBarrier = SI_TILE_BARRIER;
+constexpr int kTileProducer = SI_TILE_PRODUCER;
+constexpr int kTileMax = kTileBarrier > kTileProducer ? kTileBarrier : kTileProducer;
 constexpr int kStages = SI_STAGES;  // tile ring depth
 constexpr int kMaxRows = 512;       // stencil rows held in shared memory at once
 constexpr int kMaxW = 128;
@@ -51,6 +59,7 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // bounded device waits: 2 s
 constexpr unsigned kFlagOverflow = 1u;
 constexpr unsigned kFlagTimeout = 2u;
 constexpr unsigned kFlagBadQuery = 4u;  // a query index outside [0, n): its image is left unwritten
+constexpr unsigned kFlagLaunch = 8u;    // the kernel's shared-memory layout did not fit its launch: no work done
 
 // ------------------------------------------------------------------- grid --
 // A uniform grid over the mesh's bounding box; points counting-sorted by cell.
@@ -148,6 +157,13 @@ struct LaunchArgs {
 // warp, larger groups a block barrier per tile.
 constexpr int kModeBarrier = 1, kModeProducer = 2;
 inline int ring_mode(int log2S) { return log2S <= 2 ? kModeProducer : kModeBarrier; }
+// Disciplines compiled into the kernel instance that runs a launch whose
+// groups use `modes`: one discipline alone gets its own instance; mixed
+// launches and probe launches run the instance with both.  The launch's
+// shared-memory layout (spin_smem_bytes) follows the instance.
+inline int launch_modes(int modes, bool probe) {
+    return !probe && (modes == kModeBarrier || modes == kModeProducer) ? modes : kModeBarrier | kModeProducer;
+}
 
 // ---------------------------------------------------------- host helpers --
 // Column support threshold: v = alpha / B < W - 1  <=>  alpha^2 < ((W-1) B)^2.
@@ -160,7 +176,8 @@ Grid *mesh_grid(Mesh *m, float cell, cudaStream_t stream, si_status *st);
 float grid_cell_for(const Mesh *m, int W, float bin, int grid_div);
 int choose_log2_group(int W, int requested_group);
 size_t image_words(int W, int log2S);
-size_t spin_smem_bytes(size_t img_words);
+// Dynamic shared memory of a spin-kernel launch whose groups use `modes`.
+size_t spin_smem_bytes(size_t img_words, int modes);
 // Resident spin-kernel blocks per SM for the instance that runs `modes`.
 int blocks_per_sm_for(size_t smem_bytes, int modes);
 int num_sms(int device);

@@ -162,9 +162,10 @@ extern "C" si_status si_generate_noalloc(si_mesh_t mesh, const int32_t *query_id
     }
     const int log2S = choose_log2_group(W, schedule.group);
     const int64_t units = (m + (1 << log2S) - 1) >> log2S;
-    const size_t smem = spin_smem_bytes(image_words(W, log2S));
+    const int modes = launch_modes(ring_mode(log2S), false);
+    const size_t smem = spin_smem_bytes(image_words(W, log2S), modes);
     SI_CUDA(setup_spin_kernel_attributes(smem));
-    const int per_sm = blocks_per_sm_for(smem, ring_mode(log2S));
+    const int per_sm = blocks_per_sm_for(smem, modes);
     if (per_sm < 1) {
         set_error("si_generate_noalloc: the spin kernel does not fit on an SM");
         return SI_ERR_INVALID;
@@ -234,7 +235,7 @@ extern "C" si_status si_generate_noalloc(si_mesh_t mesh, const int32_t *query_id
     a.nitems = 1;
     a.img_words = (int)image_words(W, log2S);
     a.probe = 0;
-    a.modes = ring_mode(log2S);
+    a.modes = modes;
     launch_spin_kernel(a, a.is_static ? (int)nsteps : P, smem, st);
     note_launches(1);
     SI_CUDA(cudaGetLastError());

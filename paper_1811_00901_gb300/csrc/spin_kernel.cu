@@ -77,13 +77,22 @@ static_assert(sizeof(Header) <= kHeaderBytes, "header too large");
 constexpr int kQueryBytes = 32 * sizeof(QueryInfo);
 constexpr int kRowBytes = 3 * (kMaxRows + 4) * sizeof(int);
 constexpr int kProbeBytes = 4 * 32 * sizeof(int);
-constexpr int kTileBytes = kStages * kTile * 32;
+
+// Candidates per tile of a discipline, and the tile region of a launch.
+template <bool PMODE>
+constexpr int tile_n() {
+    return PMODE ? kTileProducer : kTileBarrier;
+}
+constexpr int tile_region_bytes(int modes) {
+    return kStages * 32 *
+           (modes == kModeBarrier ? kTileBarrier : modes == kModeProducer ? kTileProducer : kTileMax);
+}
 
 constexpr int off_query() { return kHeaderBytes; }
 constexpr int off_rows() { return off_query() + kQueryBytes; }
 constexpr int off_probe() { return off_rows() + kRowBytes; }
 constexpr int off_tiles() { return (off_probe() + kProbeBytes + 127) & ~127; }
-constexpr int off_images() { return off_tiles() + kTileBytes; }
+constexpr int off_images(int modes) { return off_tiles() + tile_region_bytes(modes); }
 
 // Exclusive scan of len[0..nr) into off[0..nr); returns the total to all threads.
 __device__ int block_scan_rows(const int *len, int *off, int nr, Header &H) {
@@ -150,9 +159,6 @@ __device__ __forceinline__ PairDist pair_dist(const float4 X, const float4 P) {
     return r;
 }
 
-// Evaluates the rest of one (query, candidate) pair and splats it when it
-// contributes.  Every contributing pair has |d|^2 < R^2 < Rc2, so the cull
-// itself is not part of the support decision.
 // fl32(x + 2^23) for 0 <= x < 2^23 has the exponent field of 2^23; its top 16
 // bits read kMagicHi + (rn(x) >> 16).
 constexpr int kMagicHi = 0x4B00;
@@ -176,7 +182,9 @@ __device__ __forceinline__ void eval_pair(const PairDist &pd, const float4 NX, c
     // alpha / B through the approximate reciprocal square root; the support
     // decision above does not depend on it, and 16-bit quantisation absorbs
     // its last-bit error
-    const float v = a2 * rsqrtf(fmaxf(a2, 1e-30f)) * k.invB;
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(fmaxf(a2, 1e-30f)));  // argument is normal
+    const float v = a2 * r * k.invB;
     // U = rn(u * 2^16): u * 2^16 is exact and below 2^23 (0 <= u < W - 1 <= 127
     // for a contributing pair), so adding 2^23 rounds it to an integer held in
     // the low 23 bits; the low 16 bits are the fraction, the top 16 the row
@@ -221,19 +229,19 @@ __device__ __forceinline__ void trip(const float4 *p0, const float4 *p1, const b
 
 // Whether a full tile (kTile candidates) of this shape takes a path without
 // per-lane range checks: compile-time shapes only.
-template <int WT, int LS, int NCONS>
+template <int WT, int LS, int NCONS, int TN>
 constexpr bool has_full_path() {
-    return WT > 0 && kTile % (2 * (NCONS == kWarps ? NCONS : 1) * (32 >> LS)) == 0;
+    return WT > 0 && TN % (2 * (NCONS == kWarps ? NCONS : 1) * (32 >> LS)) == 0;
 }
 
 // Consumes one staged tile: every lane pairs its slot's query with its
 // candidates; two candidates per lane per trip.  With FULL the tile holds
-// kTile candidates and every trip is in range:
+// TN candidates and every trip is in range:
 //  * all warps consuming (NCONS == kWarps): warp w takes trips at candidate
 //    w*cpw + 2*NCONS*cpw*t (a compile-time count, unrolled);
 //  * NCONS consumer warps: trip t covers candidates [2*cpw*t, 2*cpw*(t+1)),
 //    dealt round-robin.
-template <int WT, int LS, bool PROBE, int NCONS, bool FULL>
+template <int WT, int LS, bool PROBE, int NCONS, int TN, bool FULL>
 __device__ __forceinline__ void consume_tile(const float4 *__restrict__ tile, const int len, const int warp,
                                              const int lane, const bool active, const float4 P, const float4 N,
                                              const PairConsts &k, const Shape<WT, LS> sh, int *img_adj, int &cnt,
@@ -244,7 +252,7 @@ __device__ __forceinline__ void consume_tile(const float4 *__restrict__ tile, co
     const int stride = NCONS * cpw;
     if constexpr (FULL && NCONS == kWarps) {
         constexpr int kStride = NCONS * (32 >> LS);
-        constexpr int kTrips = kTile / (2 * kStride);
+        constexpr int kTrips = TN / (2 * kStride);
         const float4 *t0 = tile + 2 * (warp * cpw + sub);
 #pragma unroll 4
         for (int tr = 0; tr < kTrips; ++tr)
@@ -252,7 +260,7 @@ __device__ __forceinline__ void consume_tile(const float4 *__restrict__ tile, co
                                 k, sh, img_adj, cnt, pc_c, pc_s, pc_h);
     } else if constexpr (FULL) {
         constexpr int kCpw = 32 >> LS;
-        constexpr int kTrips = kTile / (2 * kCpw);
+        constexpr int kTrips = TN / (2 * kCpw);
         const float4 *t0 = tile + 2 * sub;
         for (int tr = warp; tr < kTrips; tr += NCONS)
             trip<WT, LS, PROBE>(t0 + 4 * tr * kCpw, t0 + 4 * tr * kCpw + 2 * kCpw, active, active, P, N, k, sh,
@@ -268,19 +276,19 @@ __device__ __forceinline__ void consume_tile(const float4 *__restrict__ tile, co
 }
 
 // Consumes a tile, through the range-check-free path when it is full.
-template <int WT, int LS, bool PROBE, int NCONS>
+template <int WT, int LS, bool PROBE, int NCONS, int TN>
 __device__ __forceinline__ void consume_any(const float4 *__restrict__ tile, const int len, const int warp,
                                             const int lane, const bool active, const float4 P, const float4 N,
                                             const PairConsts &k, const Shape<WT, LS> sh, int *img_adj, int &cnt,
                                             int *pc_c, int *pc_s, unsigned *pc_h) {
-    if constexpr (has_full_path<WT, LS, NCONS>()) {
-        if (len == kTile) {
-            consume_tile<WT, LS, PROBE, NCONS, true>(tile, len, warp, lane, active, P, N, k, sh, img_adj, cnt, pc_c,
+    if constexpr (has_full_path<WT, LS, NCONS, TN>()) {
+        if (len == TN) {
+            consume_tile<WT, LS, PROBE, NCONS, TN, true>(tile, len, warp, lane, active, P, N, k, sh, img_adj, cnt, pc_c,
                                                      pc_s, pc_h);
             return;
         }
     }
-    consume_tile<WT, LS, PROBE, NCONS, false>(tile, len, warp, lane, active, P, N, k, sh, img_adj, cnt, pc_c, pc_s,
+    consume_tile<WT, LS, PROBE, NCONS, TN, false>(tile, len, warp, lane, active, P, N, k, sh, img_adj, cnt, pc_c, pc_s,
                                               pc_h);
 }
 
@@ -329,6 +337,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
     const PairConsts k{it.Rc2, it.cosS, it.invB, it.halfW, it.umax, it.amax2};
     const float Rc = it.Rc;
     const int slot = lane & (S - 1);
+    constexpr int TN = tile_n<PMODE>();  // candidates per tile
     const int img_words_pad = ((S * W1 * W1) + 3) & ~3;
 
     // unit u = slice `sl` of group `g`: with K slices per group, K blocks share
@@ -439,7 +448,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
         }
         __syncthreads();
         const int total = block_scan_rows(sv.row_len, sv.row_off, nr, H);
-        const int ntiles = (total + kTile - 1) / kTile;
+        const int ntiles = (total + TN - 1) / TN;
         // this unit's share of the tiles: [tlo, tlo + nt)
         const int tlo = (int)((int64_t)ntiles * sl / K);
         const int nt = (int)((int64_t)ntiles * (sl + 1) / K) - tlo;
@@ -450,7 +459,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
             // reusing a stage once all consumer warps have released its last tile
             if (lane == 0) {
                 int cr = 0, co = 0;
-                if (nt > 0) row_cursor(sv.row_off, nr, tlo * kTile, cr, co);
+                if (nt > 0) row_cursor(sv.row_off, nr, tlo * TN, cr, co);
                 for (int tt = 0; tt < nt; ++tt) {
                     const int b = tt % kStages;
                     const int t = tlo + tt;
@@ -466,8 +475,8 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
                             break;
                         }
                     }
-                    const int need = min(kTile, total - t * kTile);
-                    float4 *dst = sv.tiles + (size_t)b * kTile * 2;
+                    const int need = min(TN, total - t * TN);
+                    float4 *dst = sv.tiles + (size_t)b * TN * 2;
                     fence_proxy_async_smem();
                     mbar_arrive_expect_tx(&H.bar[b], (uint32_t)need * 32u);
                     int done = 0;
@@ -509,9 +518,9 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
                     break;
                 }
                 phase_bits ^= 1u << b;
-                const int len = min(kTile, total - t * kTile);
+                const int len = min(TN, total - t * TN);
                 if (PROBE && tid < nq) sv.pc_examined[tid] += len;
-                consume_any<WT, LS, PROBE, kProdConsumers>(sv.tiles + (size_t)b * kTile * 2, len, warp, lane,
+                consume_any<WT, LS, PROBE, kProdConsumers, TN>(sv.tiles + (size_t)b * TN * 2, len, warp, lane,
                                                            active, qP, qN, k, sh, img_adj, cnt, sv.pc_culled + slot,
                                                            sv.pc_support + slot, sv.pc_hash + slot);
                 __syncwarp();
@@ -525,7 +534,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
         // ---- producer state (thread 0): row cursor
         if (tid == 0) {
             int cr0 = 0, co0 = 0;
-            if (nt > 0) row_cursor(sv.row_off, nr, tlo * kTile, cr0, co0);
+            if (nt > 0) row_cursor(sv.row_off, nr, tlo * TN, cr0, co0);
             H.cur_r = cr0;
             H.cur_o = co0;
         }
@@ -533,8 +542,8 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
             int cr = H.cur_r, co = H.cur_o;
             const int b = tt % kStages;
             const int t = tlo + tt;
-            const int need = min(kTile, total - t * kTile);
-            float4 *dst = sv.tiles + (size_t)b * kTile * 2;
+            const int need = min(TN, total - t * TN);
+            float4 *dst = sv.tiles + (size_t)b * TN * 2;
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&H.bar[b], (uint32_t)need * 32u);
             int done = 0;
@@ -563,9 +572,9 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
             const bool ok = mbar_wait_bounded(&H.bar[b], (phase_bits >> b) & 1u, kWaitLimitNs);
             if (ok) {
                 phase_bits ^= 1u << b;
-                const int len = min(kTile, total - (tlo + tt) * kTile);
+                const int len = min(TN, total - (tlo + tt) * TN);
                 if (PROBE && tid < nq) sv.pc_examined[tid] += len;
-                consume_any<WT, LS, PROBE, kWarps>(sv.tiles + (size_t)b * kTile * 2, len, warp, lane, active, qP,
+                consume_any<WT, LS, PROBE, kWarps, TN>(sv.tiles + (size_t)b * TN * 2, len, warp, lane, active, qP,
                                                    qN, k, sh, img_adj, cnt, sv.pc_culled + slot, sv.pc_support + slot,
                                                    sv.pc_hash + slot);
             }
@@ -666,9 +675,18 @@ __global__ void __launch_bounds__(kThreads, min_blocks_for<MODES>()) spin_kernel
     sv.pc_hash = reinterpret_cast<unsigned *>(sv.pc_support + 32);
     sv.pc_examined = sv.pc_support + 64;
     sv.tiles = reinterpret_cast<float4 *>(smem + off_tiles());
-    sv.img = reinterpret_cast<int *>(smem + off_images());
+    sv.img = reinterpret_cast<int *>(smem + off_images(MODES));
     Header &H = *sv.H;
     const int tid = threadIdx.x;
+
+    // the layout of this instance must fit the launch's dynamic shared memory
+    uint32_t dyn_bytes;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
+    if ((uint64_t)off_images(MODES) + (uint64_t)a.img_words * sizeof(int) > dyn_bytes) {
+        if (tid == 0 && blockIdx.x == 0)
+            for (int i = 0; i < a.nitems; ++i) atomicOr(a.items[i].flags, kFlagLaunch);
+        return;
+    }
 
     if (tid == 0) {
         for (int b = 0; b < kStages; ++b) {
@@ -763,7 +781,10 @@ size_t image_words(int W, int log2S) {
     return (w + 3) & ~size_t(3);
 }
 
-size_t spin_smem_bytes(size_t img_words) { return (size_t)off_images() + img_words * sizeof(int); }
+size_t spin_smem_bytes(size_t img_words, int modes) {
+    const int m = modes == kModeBarrier || modes == kModeProducer ? modes : kModeBarrier | kModeProducer;
+    return (size_t)off_images(m) + img_words * sizeof(int);
+}
 
 cudaError_t setup_spin_kernel_attributes(size_t smem_bytes) {
     static size_t done = 0;
@@ -794,6 +815,8 @@ int blocks_per_sm_for(size_t smem_bytes, int modes) {
 }
 
 void launch_spin_kernel(const LaunchArgs &a, int blocks, size_t smem, cudaStream_t stream) {
+    // a.modes is launch_modes(...) of the call, the same value its shared-memory
+    // size came from; each instance also checks its layout against the launch
     if (a.probe)
         spin_kernel<true, kModeBarrier | kModeProducer><<<blocks, kThreads, smem, stream>>>(a);
     else if (a.modes == kModeBarrier)
@@ -815,13 +838,13 @@ int choose_log2_group(int W, int requested_group) {
     const size_t budget = (size_t)SI_SMEM_BUDGET_KB * 1024;
     int l = 0;
     for (int c = 5; c > 0; --c)
-        if (spin_smem_bytes(image_words(W, c)) <= budget) {
+        if (spin_smem_bytes(image_words(W, c), ring_mode(c)) <= budget) {
             l = c;
             break;
         }
     // wide images: when three blocks per SM leave at most two images per
     // group, four images at two blocks per SM feed each tile better
-    if (l <= 1 && spin_smem_bytes(image_words(W, l + 1)) <= (size_t)113 * 1024) ++l;
+    if (l <= 1 && spin_smem_bytes(image_words(W, l + 1), ring_mode(l + 1)) <= (size_t)113 * 1024) ++l;
     return l;
 }
 
