@@ -174,7 +174,9 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
     p->modes = 0;
     for (int k = 0; k < nitems; ++k) p->modes |= ring_mode(p->log2S[k]);
     p->modes = launch_modes(p->modes, probe);
-    p->smem = spin_smem_bytes(p->max_img_words, p->modes);
+    p->smem = 0;
+    for (int k = 0; k < nitems; ++k)
+        if (items[k].m > 0) p->smem = std::max(p->smem, spin_smem_bytes(items[k].W, p->log2S[k]));
     SI_CUDA(setup_spin_kernel_attributes(p->smem));
     const int per_sm = blocks_per_sm_for(p->smem, p->modes);
     if (per_sm < 1) {

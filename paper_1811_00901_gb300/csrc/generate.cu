@@ -54,7 +54,7 @@ si_status check_item(const si_batch_item &it, const si_schedule &sc, int dev) {
         return SI_ERR_INVALID;
     }
     const int l2 = choose_log2_group(it.W, sc.group);
-    if (spin_smem_bytes(image_words(it.W, l2), ring_mode(l2)) > (size_t)227 * 1024) {
+    if (spin_smem_bytes(it.W, l2) > (size_t)227 * 1024) {
         set_error("W = %d with group %d needs more shared memory than a block has", it.W, 1 << l2);
         return SI_ERR_INVALID;
     }
@@ -97,7 +97,7 @@ si_status si_mesh_prepare(si_mesh_t mesh, int32_t W, float bin_size, const si_sc
                         &st);
     if (!g) return st;
     const int l2 = choose_log2_group(W, schedule ? schedule->group : 0);
-    SI_CUDA(setup_spin_kernel_attributes(spin_smem_bytes(image_words(W, l2), ring_mode(l2))));
+    SI_CUDA(setup_spin_kernel_attributes(spin_smem_bytes(W, l2)));
     return SI_OK;
 }
 

@@ -35,21 +35,21 @@ si_status cuda_fail(cudaError_t e, const char *what);
 #define SI_SMEM_BUDGET_KB 75
 #endif
 constexpr int kThreads = SI_THREADS;  // threads per spin-kernel block
-#ifndef SI_TILE_BARRIER
-#define SI_TILE_BARRIER 448
+#ifndef SI_TILE_MAX
+#define SI_TILE_MAX 512
 #endif
-#ifndef SI_TILE_PRODUCER
-#define SI_TILE_PRODUCER 512
+#ifndef SI_TILE_MIN
+#define SI_TILE_MIN 448
 #endif
 #ifndef SI_STAGES
 #define SI_STAGES 2
 #endif
-// Candidate points per staged tile (32 B each), per tile-ring discipline: the
-// larger the tile, the fewer block barriers or stage hand-offs per candidate;
-// the barrier ring is bounded by three blocks per SM, the producer ring by two.
-constexpr int kTileBarrier = SI_TILE_BARRIER;
-constexpr int kTileProducer = SI_TILE_PRODUCER;
-constexpr int kTileMax = kTileBarrier > kTileProducer ? kTileBarrier : kTileProducer;
+// Candidate points per staged tile (32 B each): the larger the tile, the fewer
+// block barriers or stage hand-offs per candidate.  Each group shape takes the
+// largest tile in [kTileMin, kTileMax] that keeps its blocks-per-SM target
+// (tile_for_shape in spin_kernel.cu).
+constexpr int kTileMax = SI_TILE_MAX;
+constexpr int kTileMin = SI_TILE_MIN;
 constexpr int kStages = SI_STAGES;  // tile ring depth
 constexpr int kMaxRows = 512;       // stencil rows held in shared memory at once
 constexpr int kMaxW = 128;
@@ -159,8 +159,7 @@ constexpr int kModeBarrier = 1, kModeProducer = 2;
 inline int ring_mode(int log2S) { return log2S <= 2 ? kModeProducer : kModeBarrier; }
 // Disciplines compiled into the kernel instance that runs a launch whose
 // groups use `modes`: one discipline alone gets its own instance; mixed
-// launches and probe launches run the instance with both.  The launch's
-// shared-memory layout (spin_smem_bytes) follows the instance.
+// launches and probe launches run the instance with both.
 inline int launch_modes(int modes, bool probe) {
     return !probe && (modes == kModeBarrier || modes == kModeProducer) ? modes : kModeBarrier | kModeProducer;
 }
@@ -176,8 +175,9 @@ Grid *mesh_grid(Mesh *m, float cell, cudaStream_t stream, si_status *st);
 float grid_cell_for(const Mesh *m, int W, float bin, int grid_div);
 int choose_log2_group(int W, int requested_group);
 size_t image_words(int W, int log2S);
-// Dynamic shared memory of a spin-kernel launch whose groups use `modes`.
-size_t spin_smem_bytes(size_t img_words, int modes);
+// Dynamic shared memory a group of shape (W, 2^log2S images) needs in the
+// spin kernel; a launch takes the maximum over its items.
+size_t spin_smem_bytes(int W, int log2S);
 // Resident spin-kernel blocks per SM for the instance that runs `modes`.
 int blocks_per_sm_for(size_t smem_bytes, int modes);
 int num_sms(int device);

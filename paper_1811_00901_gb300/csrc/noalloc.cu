@@ -163,7 +163,7 @@ extern "C" si_status si_generate_noalloc(si_mesh_t mesh, const int32_t *query_id
     const int log2S = choose_log2_group(W, schedule.group);
     const int64_t units = (m + (1 << log2S) - 1) >> log2S;
     const int modes = launch_modes(ring_mode(log2S), false);
-    const size_t smem = spin_smem_bytes(image_words(W, log2S), modes);
+    const size_t smem = spin_smem_bytes(W, log2S);
     SI_CUDA(setup_spin_kernel_attributes(smem));
     const int per_sm = blocks_per_sm_for(smem, modes);
     if (per_sm < 1) {

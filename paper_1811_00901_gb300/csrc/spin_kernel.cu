@@ -78,21 +78,29 @@ constexpr int kQueryBytes = 32 * sizeof(QueryInfo);
 constexpr int kRowBytes = 3 * (kMaxRows + 4) * sizeof(int);
 constexpr int kProbeBytes = 4 * 32 * sizeof(int);
 
-// Candidates per tile of a discipline, and the tile region of a launch.
-template <bool PMODE>
-constexpr int tile_n() {
-    return PMODE ? kTileProducer : kTileBarrier;
-}
-constexpr int tile_region_bytes(int modes) {
-    return kStages * 32 *
-           (modes == kModeBarrier ? kTileBarrier : modes == kModeProducer ? kTileProducer : kTileMax);
-}
-
+// Shared-memory layout of a block: header, queries, stencil rows, probe
+// counters, then per group the tile ring (kStages x tile) and the images.
 constexpr int off_query() { return kHeaderBytes; }
 constexpr int off_rows() { return off_query() + kQueryBytes; }
 constexpr int off_probe() { return off_rows() + kRowBytes; }
 constexpr int off_tiles() { return (off_probe() + kProbeBytes + 127) & ~127; }
-constexpr int off_images(int modes) { return off_tiles() + tile_region_bytes(modes); }
+
+constexpr int img_words_of(int W, int log2S) { return ((((W + 1) * (W + 1)) << log2S) + 3) & ~3; }
+constexpr int shape_smem(int W, int log2S, int tn) {
+    return off_tiles() + kStages * 32 * tn + 4 * img_words_of(W, log2S);
+}
+
+// Candidates per tile for a group shape.  Producer-ring shapes (<= 4 images)
+// run two blocks per SM and take kTileMax.  Block-barrier shapes take the
+// largest tile, a whole number of unrolled trips (2 x 8 warps x 32/S
+// candidates), that keeps three blocks per SM, else kTileMax.
+constexpr int tile_for_shape(int W, int log2S) {
+    if (log2S <= 2) return kTileMax;
+    const int unit = 2 * kWarps * (32 >> log2S);
+    for (int tn = kTileMax; tn >= kTileMin; tn -= 16)
+        if (tn % unit == 0 && shape_smem(W, log2S, tn) <= SI_SMEM_BUDGET_KB * 1024) return tn;
+    return kTileMax;
+}
 
 // Exclusive scan of len[0..nr) into off[0..nr); returns the total to all threads.
 __device__ int block_scan_rows(const int *len, int *off, int nr, Header &H) {
@@ -231,7 +239,7 @@ __device__ __forceinline__ void trip(const float4 *p0, const float4 *p1, const b
 // per-lane range checks: compile-time shapes only.
 template <int WT, int LS, int NCONS, int TN>
 constexpr bool has_full_path() {
-    return WT > 0 && TN % (2 * (NCONS == kWarps ? NCONS : 1) * (32 >> LS)) == 0;
+    return WT > 0 && TN > 0 && TN % (2 * (NCONS == kWarps ? NCONS : 1) * (32 >> LS)) == 0;
 }
 
 // Consumes one staged tile: every lane pairs its slot's query with its
@@ -275,7 +283,8 @@ __device__ __forceinline__ void consume_tile(const float4 *__restrict__ tile, co
     }
 }
 
-// Consumes a tile, through the range-check-free path when it is full.
+// Consumes a tile, through the range-check-free path when it holds TN
+// candidates (TN = 0: shapes known only at run time, no such path).
 template <int WT, int LS, bool PROBE, int NCONS, int TN>
 __device__ __forceinline__ void consume_any(const float4 *__restrict__ tile, const int len, const int warp,
                                             const int lane, const bool active, const float4 P, const float4 N,
@@ -299,7 +308,7 @@ struct SmemView {
     int *pc_culled, *pc_support, *pc_examined;
     unsigned *pc_hash;
     float4 *tiles;
-    int *img;
+    uint32_t dyn_bytes;  // dynamic shared memory of the launch
 };
 
 // Row and offset of flat candidate position `first` in a row list with
@@ -337,7 +346,15 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
     const PairConsts k{it.Rc2, it.cosS, it.invB, it.halfW, it.umax, it.amax2};
     const float Rc = it.Rc;
     const int slot = lane & (S - 1);
-    constexpr int TN = tile_n<PMODE>();  // candidates per tile
+    // candidates per tile: a compile-time constant for the specialised shapes
+    constexpr int TNC = WT > 0 ? tile_for_shape(WT, LS) : 0;
+    const int TN = WT > 0 ? TNC : tile_for_shape(W, sh.log2S());
+    int *const img = reinterpret_cast<int *>(sv.tiles + (size_t)kStages * TN * 2);
+    if ((uint32_t)shape_smem(W, sh.log2S(), TN) > sv.dyn_bytes) {
+        // the launch's shared memory does not hold this shape (an internal error)
+        if (tid == 0) atomicOr(it.flags, kFlagLaunch);
+        return true;
+    }
     const int img_words_pad = ((S * W1 * W1) + 3) & ~3;
 
     // unit u = slice `sl` of group `g`: with K slices per group, K blocks share
@@ -375,7 +392,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
         sv.pc_examined[tid] = 0;
     }
     {
-        int4 *z4 = reinterpret_cast<int4 *>(sv.img);
+        int4 *z4 = reinterpret_cast<int4 *>(img);
         for (int w = tid; w < img_words_pad / 4; w += kThreads) z4[w] = make_int4(0, 0, 0, 0);
     }
     __syncthreads();
@@ -417,7 +434,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
     const float4 qN = Q[slot].n;
     const bool active = slot < nq;
     int cnt = 0;
-    int *img_adj = sv.img + slot - kMagicHi * (sh.row_words() + S);
+    int *img_adj = img + slot - kMagicHi * (sh.row_words() + S);
     const int ylo = H.ylo, zlo = H.zlo;
     const int ny = H.yhi - ylo + 1, nz = H.zhi - zlo + 1;
     const int nrows_total = ny * nz;
@@ -520,7 +537,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
                 phase_bits ^= 1u << b;
                 const int len = min(TN, total - t * TN);
                 if (PROBE && tid < nq) sv.pc_examined[tid] += len;
-                consume_any<WT, LS, PROBE, kProdConsumers, TN>(sv.tiles + (size_t)b * TN * 2, len, warp, lane,
+                consume_any<WT, LS, PROBE, kProdConsumers, TNC>(sv.tiles + (size_t)b * TN * 2, len, warp, lane,
                                                            active, qP, qN, k, sh, img_adj, cnt, sv.pc_culled + slot,
                                                            sv.pc_support + slot, sv.pc_hash + slot);
                 __syncwarp();
@@ -574,7 +591,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
                 phase_bits ^= 1u << b;
                 const int len = min(TN, total - (tlo + tt) * TN);
                 if (PROBE && tid < nq) sv.pc_examined[tid] += len;
-                consume_any<WT, LS, PROBE, kWarps, TN>(sv.tiles + (size_t)b * TN * 2, len, warp, lane, active, qP,
+                consume_any<WT, LS, PROBE, kWarps, TNC>(sv.tiles + (size_t)b * TN * 2, len, warp, lane, active, qP,
                                                    qN, k, sh, img_adj, cnt, sv.pc_culled + slot, sv.pc_support + slot,
                                                    sv.pc_hash + slot);
             }
@@ -605,7 +622,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
         if (q >= nq) continue;
         const int p = e >> sh.log2S();
         const int i = p / W, j = p - i * W;
-        const int v = sv.img[(i * W1 + j) * S + q];
+        const int v = img[(i * W1 + j) * S + q];
         const int qs = Q[q].slot;
         if (qs >= 0) {
             if (K == 1)
@@ -675,18 +692,10 @@ __global__ void __launch_bounds__(kThreads, min_blocks_for<MODES>()) spin_kernel
     sv.pc_hash = reinterpret_cast<unsigned *>(sv.pc_support + 32);
     sv.pc_examined = sv.pc_support + 64;
     sv.tiles = reinterpret_cast<float4 *>(smem + off_tiles());
-    sv.img = reinterpret_cast<int *>(smem + off_images(MODES));
     Header &H = *sv.H;
     const int tid = threadIdx.x;
 
-    // the layout of this instance must fit the launch's dynamic shared memory
-    uint32_t dyn_bytes;
-    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
-    if ((uint64_t)off_images(MODES) + (uint64_t)a.img_words * sizeof(int) > dyn_bytes) {
-        if (tid == 0 && blockIdx.x == 0)
-            for (int i = 0; i < a.nitems; ++i) atomicOr(a.items[i].flags, kFlagLaunch);
-        return;
-    }
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(sv.dyn_bytes));
 
     if (tid == 0) {
         for (int b = 0; b < kStages; ++b) {
@@ -781,10 +790,7 @@ size_t image_words(int W, int log2S) {
     return (w + 3) & ~size_t(3);
 }
 
-size_t spin_smem_bytes(size_t img_words, int modes) {
-    const int m = modes == kModeBarrier || modes == kModeProducer ? modes : kModeBarrier | kModeProducer;
-    return (size_t)off_images(m) + img_words * sizeof(int);
-}
+size_t spin_smem_bytes(int W, int log2S) { return (size_t)shape_smem(W, log2S, tile_for_shape(W, log2S)); }
 
 cudaError_t setup_spin_kernel_attributes(size_t smem_bytes) {
     static size_t done = 0;
@@ -815,8 +821,7 @@ int blocks_per_sm_for(size_t smem_bytes, int modes) {
 }
 
 void launch_spin_kernel(const LaunchArgs &a, int blocks, size_t smem, cudaStream_t stream) {
-    // a.modes is launch_modes(...) of the call, the same value its shared-memory
-    // size came from; each instance also checks its layout against the launch
+    // a.modes is launch_modes(...) of the call
     if (a.probe)
         spin_kernel<true, kModeBarrier | kModeProducer><<<blocks, kThreads, smem, stream>>>(a);
     else if (a.modes == kModeBarrier)
@@ -838,13 +843,13 @@ int choose_log2_group(int W, int requested_group) {
     const size_t budget = (size_t)SI_SMEM_BUDGET_KB * 1024;
     int l = 0;
     for (int c = 5; c > 0; --c)
-        if (spin_smem_bytes(image_words(W, c), ring_mode(c)) <= budget) {
+        if (spin_smem_bytes(W, c) <= budget) {
             l = c;
             break;
         }
     // wide images: when three blocks per SM leave at most two images per
     // group, four images at two blocks per SM feed each tile better
-    if (l <= 1 && spin_smem_bytes(image_words(W, l + 1), ring_mode(l + 1)) <= (size_t)113 * 1024) ++l;
+    if (l <= 1 && spin_smem_bytes(W, l + 1) <= (size_t)113 * 1024) ++l;
     return l;
 }
 

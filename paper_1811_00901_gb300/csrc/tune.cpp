@@ -106,7 +106,7 @@ si_status si_tune_mesh(si_mesh_t mesh, const int32_t *query_idx, int64_t m, int3
         }
     // stage 2: loop rule x minimum chunk x worker count
     const int l2 = choose_log2_group(W, cur.group);
-    const size_t smem = spin_smem_bytes(image_words(W, l2), ring_mode(l2));
+    const size_t smem = spin_smem_bytes(W, l2);
     const int per_sm = std::max(1, blocks_per_sm_for(smem, ring_mode(l2)));
     const int sms = num_sms(dev);
     const int worker_opts[] = {0, sms * per_sm / 2, sms * per_sm * 2};
