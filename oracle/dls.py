@@ -19,6 +19,16 @@ getChunk(DM, schedulingStep, N, workersCount) and hands out the range
   rule, R = iterations remaining when the batch starts), never below
   ``min_chunk``.
 
+* FAC_PROB -- factoring with the batch size of its original probabilistic
+  rule (Hummel, Schonberg and Flynn 1992, the paper's reference for FAC),
+  for iterations whose times have coefficient of variation cov = sigma / mu:
+  at the start of batch j, with R_j iterations remaining,
+  b_j = P / (2 sqrt(R_j)) * cov, x_0 = 1 + b_0^2 + b_0 sqrt(b_0^2 + 2),
+  x_j = 2 + b_j^2 + b_j sqrt(b_j^2 + 4) for j >= 1, and the batch hands out
+  P chunks of ceil(R_j / (x_j P)), never below ``min_chunk``.  The rule's
+  quantities are real numbers; they are evaluated in IEEE double in this
+  order, and the ceiling taken of the double quotient.
+
 Readings common to all rules (Algorithm 3 leaves both implicit): the
 scheduling step advances by one per assignment, and every chunk is clamped to
 the iterations that remain.  ``min_chunk`` (>= 1) is a lower bound on the
@@ -26,19 +36,31 @@ chunk of SS, GSS and FAC; SS with ``min_chunk = k`` hands out k iterations per
 request.
 """
 
-STATIC, SS, GSS, FAC = 0, 1, 2, 3
-NAMES = {STATIC: "STATIC", SS: "SS", GSS: "GSS", FAC: "FAC"}
+import math
+
+STATIC, SS, GSS, FAC, FAC_PROB = 0, 1, 2, 3, 4
+NAMES = {STATIC: "STATIC", SS: "SS", GSS: "GSS", FAC: "FAC", FAC_PROB: "FAC_PROB"}
 
 
 def _ceil_div(a, b):
     return -(-a // b)
 
 
-def get_chunk(kind, step, remaining, n, workers, min_chunk=1, fac_batch=None):
+def fac_prob_batch_chunk(batch, remaining, workers, cov):
+    """The probabilistic factoring chunk of batch ``batch`` (see FAC_PROB)."""
+    b = workers / (2.0 * math.sqrt(remaining)) * cov
+    if batch == 0:
+        x = 1.0 + b * b + b * math.sqrt(b * b + 2.0)
+    else:
+        x = 2.0 + b * b + b * math.sqrt(b * b + 4.0)
+    return int(math.ceil(remaining / (x * workers)))
+
+
+def get_chunk(kind, step, remaining, n, workers, min_chunk=1, fac_batch=None, cov=0.0):
     """Chunk size for one scheduling step (Algorithm 3's getChunk).
 
     ``fac_batch`` carries the FAC batch chunk between calls: a dict that the
-    caller keeps for the whole loop.
+    caller keeps for the whole loop.  ``cov`` is FAC_PROB's sigma / mu.
     """
     min_chunk = max(1, int(min_chunk))
     if kind == STATIC:
@@ -52,12 +74,16 @@ def get_chunk(kind, step, remaining, n, workers, min_chunk=1, fac_batch=None):
         if step % workers == 0:
             fac_batch["c"] = max(min_chunk, _ceil_div(remaining, 2 * workers))
         chunk = fac_batch["c"]
+    elif kind == FAC_PROB:
+        if step % workers == 0:
+            fac_batch["c"] = max(min_chunk, fac_prob_batch_chunk(step // workers, remaining, workers, cov))
+        chunk = fac_batch["c"]
     else:
         raise ValueError("unknown schedule kind %r" % (kind,))
     return min(chunk, remaining)
 
 
-def chunk_sequence(kind, n, workers, min_chunk=1):
+def chunk_sequence(kind, n, workers, min_chunk=1, cov=0.0):
     """The master loop of Algorithm 3 run to completion, without workers.
 
     Returns the list of chunk sizes in the order they are handed out.  For
@@ -76,16 +102,16 @@ def chunk_sequence(kind, n, workers, min_chunk=1):
             scheduled += sizes[-1]
         return sizes
     while scheduled < n:
-        c = get_chunk(kind, step, n - scheduled, n, workers, min_chunk, state)
+        c = get_chunk(kind, step, n - scheduled, n, workers, min_chunk, state, cov)
         sizes.append(c)
         scheduled += c
         step += 1
     return sizes
 
 
-def chunk_starts(kind, n, workers, min_chunk=1):
+def chunk_starts(kind, n, workers, min_chunk=1, cov=0.0):
     """Prefix form: starts[s] .. starts[s + 1] is the range of step s."""
     starts = [0]
-    for c in chunk_sequence(kind, n, workers, min_chunk):
+    for c in chunk_sequence(kind, n, workers, min_chunk, cov):
         starts.append(starts[-1] + c)
     return starts
