@@ -72,8 +72,23 @@ typedef enum si_sched_kind {
     SI_SCHED_STATIC = 0, /* worker k takes groups [floor(kU/P), floor((k+1)U/P)), no atomics */
     SI_SCHED_SS = 1,     /* one group (min_chunk groups) per request */
     SI_SCHED_GSS = 2,    /* ceil(remaining / P) groups per request, >= min_chunk */
-    SI_SCHED_FAC = 3     /* batches of P equal chunks of ceil(remaining / (2P)), >= min_chunk */
+    SI_SCHED_FAC = 3,    /* batches of P equal chunks of ceil(remaining / (2P)), >= min_chunk */
+    SI_SCHED_FAC_PROB = 4 /* factoring with the batch size of its original probabilistic rule
+                             (Hummel, Schonberg and Flynn, 1992 -- the paper's reference for FAC):
+                             batch j hands out P chunks of ceil(R_j / (x_j P)), R_j what remains,
+                             b_j = P / (2 sqrt(R_j)) * cov, x_0 = 1 + b_0^2 + b_0 sqrt(b_0^2 + 2),
+                             x_j = 2 + b_j^2 + b_j sqrt(b_j^2 + 4) (j >= 1), cov = sigma / mu of the
+                             iteration time (si_schedule.fac_cov), evaluated in IEEE double;
+                             >= min_chunk */
 } si_sched_kind;
+
+/* How a contributing pair is counted into its image. */
+typedef enum si_binning {
+    SI_BIN_BILINEAR = 0, /* weight 1 split over the four pixels around (u, v), fixed point x 65536 */
+    SI_BIN_NEAREST = 1   /* Algorithm 1's own count: pixel (ceil(u), ceil(v)) += 1 for
+                            0 <= ceil(u), ceil(v) <= W - 1, evaluated in IEEE FP32 as specified
+                            at si_generate */
+} si_binning;
 
 /* Scheduling and launch shape.  Zero fields mean "choose automatically". */
 typedef struct si_schedule {
@@ -86,6 +101,15 @@ typedef struct si_schedule {
                             its partial images into `out` with integer atomics (results are
                             unchanged).  0 -> auto: 1 when the call has enough groups to fill
                             the GPU, more for calls with few groups (small requests). */
+    int32_t binning;     /* si_binning (0 -> bilinear) */
+    int32_t slow_workers;/* heterogeneity emulation (the paper's Type1 + Type2 runs, Sec. 5.2):
+                            workers 0 .. slow_workers-1 are slow.  They request first -- worker
+                            k < slow_workers takes scheduling step k -- and after each step a slow
+                            worker idles (slowdown - 1) x the time the step took (at most 1 s).
+                            Results are unchanged.  0 -> no emulation.  For batched calls the
+                            emulation comes from the override (or the first item's rule). */
+    float slowdown;      /* >= 1 (0 -> 1) */
+    float fac_cov;       /* SI_SCHED_FAC_PROB: sigma / mu of an iteration's time, finite, >= 0 */
 } si_schedule;
 
 /* Optional per-image probes (device buffers of m entries, each may be NULL).
@@ -194,6 +218,8 @@ si_status si_generate_host(const float *points, const float *normals, int64_t n,
  *   needing more steps is SI_ERR_INVALID (raise min_chunk or group).
  *   The mesh's grid for this W, bin size and grid_div must exist already
  *   (si_mesh_prepare); otherwise SI_ERR_INVALID.
+ *   Schedules: STATIC, SS, GSS or FAC with bilinear binning and no slow
+ *   workers; anything else is SI_ERR_INVALID.
  *   The first call on a device (with it current) looks up the array's device
  *   address; make that first call before any stream capture.
  *   Calls share the array: two calls whose work overlaps on the GPU race. */
@@ -210,6 +236,12 @@ si_status si_generate_noalloc(si_mesh_t mesh, const int32_t *query_idx, int64_t 
  * SI_ERR_INVALID is returned. */
 si_status si_chunk_table(int32_t kind, int64_t units, int32_t workers, int32_t min_chunk,
                          int64_t *starts, int64_t capacity, int64_t *nsteps);
+
+/* si_chunk_table for a whole schedule (kind, min_chunk and, for
+ * SI_SCHED_FAC_PROB, fac_cov); si_chunk_table(kind, ...) is this with
+ * fac_cov = 0. */
+si_status si_schedule_chunks(const si_schedule *schedule, int64_t units, int32_t workers, int64_t *starts,
+                             int64_t capacity, int64_t *nsteps);
 
 /* The FP32 candidate threshold Rc2 = fl32(R^2 (1 + 1e-5)), R^2 = h^2 +
  * ((W-1)B)^2, h = W B / 2: every contributing X has |X-P|^2 < R^2, and the

@@ -15,8 +15,11 @@ LIB_PATH = os.path.join(HERE, "_lib", "libspin_gb300.so")
 SI_OK, SI_ERR_INVALID, SI_ERR_CUDA, SI_ERR_OOM, SI_ERR_OVERFLOW, SI_ERR_TIMEOUT, SI_ERR_BUSY = range(7)
 STATUS_NAMES = {0: "SI_OK", 1: "SI_ERR_INVALID", 2: "SI_ERR_CUDA", 3: "SI_ERR_OOM", 4: "SI_ERR_OVERFLOW",
                 5: "SI_ERR_TIMEOUT", 6: "SI_ERR_BUSY"}
-SI_SCHED_STATIC, SI_SCHED_SS, SI_SCHED_GSS, SI_SCHED_FAC = range(4)
-SCHED_NAMES = {"STATIC": SI_SCHED_STATIC, "SS": SI_SCHED_SS, "GSS": SI_SCHED_GSS, "FAC": SI_SCHED_FAC}
+SI_SCHED_STATIC, SI_SCHED_SS, SI_SCHED_GSS, SI_SCHED_FAC, SI_SCHED_FAC_PROB = range(5)
+SCHED_NAMES = {"STATIC": SI_SCHED_STATIC, "SS": SI_SCHED_SS, "GSS": SI_SCHED_GSS, "FAC": SI_SCHED_FAC,
+               "FAC_PROB": SI_SCHED_FAC_PROB}
+SI_BIN_BILINEAR, SI_BIN_NEAREST = 0, 1
+BIN_NAMES = {"BILINEAR": SI_BIN_BILINEAR, "NEAREST": SI_BIN_NEAREST}
 
 
 class SpinError(RuntimeError):
@@ -27,7 +30,9 @@ class SpinError(RuntimeError):
 
 class si_schedule(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("min_chunk", ctypes.c_int32), ("num_workers", ctypes.c_int32),
-                ("group", ctypes.c_int32), ("grid_div", ctypes.c_int32), ("slices", ctypes.c_int32)]
+                ("group", ctypes.c_int32), ("grid_div", ctypes.c_int32), ("slices", ctypes.c_int32),
+                ("binning", ctypes.c_int32), ("slow_workers", ctypes.c_int32), ("slowdown", ctypes.c_float),
+                ("fac_cov", ctypes.c_float)]
 
 
 class si_probe(ctypes.Structure):
@@ -66,6 +71,9 @@ _SIGNATURES = {
     "si_chunk_table":([ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                         ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)],
                        ctypes.c_int),
+    "si_schedule_chunks": ([ctypes.POINTER(si_schedule), ctypes.c_int64, ctypes.c_int32,
+                            ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)],
+                           ctypes.c_int),
     "si_candidate_rc2": ([ctypes.c_int32, ctypes.c_float], ctypes.c_float),
     "si_get_stats": ([_P, ctypes.POINTER(si_stats)], ctypes.c_int),
     "si_reset_stats": ([_P], ctypes.c_int),
@@ -138,10 +146,14 @@ def _ptr(t):
     return t.data_ptr()
 
 
-def make_schedule(kind="GSS", min_chunk=1, num_workers=0, group=0, grid_div=0, slices=0):
+def make_schedule(kind="GSS", min_chunk=1, num_workers=0, group=0, grid_div=0, slices=0, binning=0,
+                  slow_workers=0, slowdown=0.0, fac_cov=0.0):
     if isinstance(kind, str):
         kind = SCHED_NAMES[kind.upper()]
-    return si_schedule(int(kind), int(min_chunk), int(num_workers), int(group), int(grid_div), int(slices))
+    if isinstance(binning, str):
+        binning = BIN_NAMES[binning.upper()]
+    return si_schedule(int(kind), int(min_chunk), int(num_workers), int(group), int(grid_div), int(slices),
+                       int(binning), int(slow_workers), float(slowdown), float(fac_cov))
 
 
 # ----------------------------------------------------------------------------
@@ -214,6 +226,16 @@ def si_chunk_table(kind, units, workers, min_chunk=1):
     buf = (ctypes.c_int64 * cap)()
     _check(load().si_chunk_table(int(kind), int(units), int(workers), int(min_chunk), buf, cap,
                                  ctypes.byref(nsteps)))
+    return list(buf)
+
+
+def si_schedule_chunks(schedule, units, workers):
+    nsteps = ctypes.c_int64()
+    load().si_schedule_chunks(ctypes.byref(schedule), int(units), int(workers), None, 0, ctypes.byref(nsteps))
+    cap = nsteps.value + 1
+    buf = (ctypes.c_int64 * cap)()
+    _check(load().si_schedule_chunks(ctypes.byref(schedule), int(units), int(workers), buf, cap,
+                                     ctypes.byref(nsteps)))
     return list(buf)
 
 

@@ -248,7 +248,7 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
         std::vector<int64_t> st;
         for (int k : order) {
             if (p->units[k] == 0) continue;
-            chunk_table(scheds[k].kind, p->units[k], workers, scheds[k].min_chunk, &st);
+            chunk_table(scheds[k].kind, p->units[k], workers, scheds[k].min_chunk, scheds[k].fac_cov, &st);
             for (size_t s = 0; s + 1 < st.size(); ++s) {
                 if (st[s + 1] == st[s]) continue;
                 p->pieces.push_back(Piece{k, (int)st[s], (int)st[s + 1], 0});

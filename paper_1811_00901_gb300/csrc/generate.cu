@@ -47,10 +47,17 @@ si_status check_item(const si_batch_item &it, const si_schedule &sc, int dev) {
         set_error("NULL output");
         return SI_ERR_INVALID;
     }
-    if (sc.kind < SI_SCHED_STATIC || sc.kind > SI_SCHED_FAC || sc.min_chunk < 0 || sc.num_workers < 0 ||
+    if (sc.kind < SI_SCHED_STATIC || sc.kind > SI_SCHED_FAC_PROB || sc.min_chunk < 0 || sc.num_workers < 0 ||
         !valid_group(sc.group) || sc.grid_div < 0 || sc.grid_div > 16 || sc.slices < 0 || sc.slices > 64) {
         set_error("bad schedule (kind %d, min_chunk %d, workers %d, group %d, grid_div %d)", sc.kind, sc.min_chunk,
                   sc.num_workers, sc.group, sc.grid_div);
+        return SI_ERR_INVALID;
+    }
+    if ((sc.binning != SI_BIN_BILINEAR && sc.binning != SI_BIN_NEAREST) || sc.slow_workers < 0 ||
+        !(sc.slowdown == 0.0f || (sc.slowdown >= 1.0f && sc.slowdown <= 1000.0f)) ||
+        !(sc.fac_cov >= 0.0f && sc.fac_cov <= 1e6f)) {
+        set_error("bad schedule (binning %d, slow_workers %d, slowdown %g, fac_cov %g)", sc.binning,
+                  sc.slow_workers, (double)sc.slowdown, (double)sc.fac_cov);
         return SI_ERR_INVALID;
     }
     const int l2 = choose_log2_group(it.W, sc.group);

@@ -183,7 +183,8 @@ int blocks_per_sm_for(size_t smem_bytes, int modes);
 int num_sms(int device);
 
 // Chunk rules (host side, one implementation for every caller).
-int64_t chunk_table(int kind, int64_t units, int workers, int min_chunk, std::vector<int64_t> *starts);
+int64_t chunk_table(int kind, int64_t units, int workers, int min_chunk, double cov,
+                    std::vector<int64_t> *starts);
 
 // Synchronous argument checks of one item.
 si_status check_item(const si_batch_item &it, const si_schedule &sc, int dev);

@@ -3,6 +3,7 @@ declares; host-only entry points agree with the oracle (no GPU needed)."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 from oracle import dls
@@ -54,6 +55,19 @@ def test_library_chunk_tables_match_oracle(lib, kind, units, workers, mc):
     assert got == expect
 
 
+@pytest.mark.parametrize("cov", [0.0, 0.25, 0.7, 1.0, 3.5, 100.0])
+@pytest.mark.parametrize("units,workers,mc", [(1000, 4, 1), (12_500, 456, 1), (100_000, 304, 2), (7, 64, 1),
+                                              (0, 8, 1), (250_000, 1, 1)])
+def test_library_fac_prob_tables_match_oracle(lib, cov, units, workers, mc):
+    """Probabilistic factoring: both sides evaluate the rule in IEEE double,
+    from the same FP32 value of cov."""
+    import paper_1811_00901_gb300 as spin
+    c32 = float(np.float32(cov))
+    expect = dls.chunk_starts(dls.FAC_PROB, units, workers, mc, cov=c32)
+    got = spin.si_schedule_chunks(spin.make_schedule("FAC_PROB", min_chunk=mc, fac_cov=cov), units, workers)
+    assert got == expect
+
+
 def test_candidate_threshold_matches_oracle(lib):
     import oracle
     import paper_1811_00901_gb300 as spin
@@ -67,6 +81,11 @@ def test_invalid_chunk_table_args(lib):
     assert lib.si_chunk_table(9, 10, 2, 1, None, 0, ctypes.byref(n)) != 0
     assert lib.si_chunk_table(0, 10, 0, 1, None, 0, ctypes.byref(n)) != 0
     assert lib.si_last_error()
+    import paper_1811_00901_gb300 as spin
+    bad = spin.make_schedule("FAC_PROB", fac_cov=-1.0)
+    assert lib.si_schedule_chunks(ctypes.byref(bad), 10, 2, None, 0, ctypes.byref(n)) != 0
+    bad = spin.make_schedule("FAC_PROB", fac_cov=float("nan"))
+    assert lib.si_schedule_chunks(ctypes.byref(bad), 10, 2, None, 0, ctypes.byref(n)) != 0
 
 
 def test_tuning_table_json_round_trip(lib, tmp_path):
