@@ -48,6 +48,10 @@ def _load():
     lib.oracle_candidates_fp32.argtypes = [f32p, ctypes.c_int64, i32p, ctypes.c_int64,
                                            ctypes.c_int32, ctypes.c_float, i64p, u32p]
     lib.oracle_candidates_fp32.restype = ctypes.c_int
+    lib.oracle_spin_images_nearest.argtypes = [f32p, f32p, ctypes.c_int64, i32p, ctypes.c_int64, ctypes.c_int32,
+                                               ctypes.c_float, ctypes.c_float, i32p,
+                                               ctypes.POINTER(ctypes.c_int64), f32p]
+    lib.oracle_spin_images_nearest.restype = ctypes.c_int
     lib.oracle_support_radius2.argtypes = [ctypes.c_int32, ctypes.c_float]
     lib.oracle_support_radius2.restype = ctypes.c_double
     lib.oracle_candidate_rc2.argtypes = [ctypes.c_int32, ctypes.c_float]
@@ -125,6 +129,26 @@ def candidates_fp32(points, W, bin_size, query_idx=None, m=None):
     if rc != 0:
         raise ValueError("oracle_candidates_fp32 failed with code %d" % rc)
     return cnt, hs
+
+
+def spin_images_nearest(points, normals, W, bin_size, cos_s, query_idx=None, m=None):
+    """Algorithm 1's own count in IEEE FP32 (see oracle_spin_images_nearest).
+
+    Returns ``(counts[m, W, W] int32, support[m] int64, max_d2[m] float32)``.
+    """
+    p, nr = _f32x3(points), _f32x3(normals)
+    n = p.shape[0]
+    q, m = _queries(query_idx, n if m is None else m)
+    cnt = np.zeros((m, W, W), dtype=np.int32)
+    sup = np.zeros(m, dtype=np.int64)
+    dmax = np.zeros(m, dtype=np.float32)
+    rc = _load().oracle_spin_images_nearest(_ptr(p, ctypes.c_float), _ptr(nr, ctypes.c_float), n,
+                                            _ptr(q, ctypes.c_int32), m, int(W), float(bin_size), float(cos_s),
+                                            _ptr(cnt, ctypes.c_int32), _ptr(sup, ctypes.c_int64),
+                                            _ptr(dmax, ctypes.c_float))
+    if rc != 0:
+        raise ValueError("oracle_spin_images_nearest failed with code %d" % rc)
+    return cnt, sup, dmax
 
 
 def support_radius2(W, bin_size):

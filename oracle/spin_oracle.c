@@ -264,3 +264,90 @@ int oracle_candidates_fp32(const float *points, int64_t n,
     }
     return OR_OK;
 }
+
+/*
+ * Algorithm 1's own count ("nearest-bin" binning, the paper-literal form):
+ * pixel (k, l) = (ceil(u), ceil(v)) of every pair that passes the angle test
+ * gets 1 when 0 <= k <= W-1 and 0 <= l <= W-1, with u = W/2 - beta/B (the
+ * half-height reading of Algorithm 1's W/2) and v = alpha/B.
+ *
+ * Precision.  ceil() turns a rounded coordinate into a pixel index, so this
+ * function and the GPU take that decision in the same precision: IEEE FP32
+ * (round to nearest even), every operation in this order (compile with
+ * -ffp-contract=off so that only the fmaf calls written here fuse):
+ *   unit normal   l2 = fmaf(nz, nz, fmaf(ny, ny, nx*nx)); s = sqrtf(l2);
+ *                 inv = 1/s; n = (nx*inv, ny*inv, nz*inv)
+ *   d             = X - P componentwise; |d|^2 = fmaf(dz, dz, fmaf(dy, dy, dx*dx))
+ *   angle         fmaf(n.z, nX.z, fmaf(n.y, nX.y, n.x*nX.x)) >= cos S
+ *   beta          = fmaf(n.z, dz, fmaf(n.y, dy, n.x*dx))
+ *   alpha         = sqrtf(max(fmaf(-beta, beta, |d|^2), 0))
+ *   u             = W/2 - beta/B;  v = alpha/B  (correctly rounded division)
+ *   k, l          = ceilf(u), ceilf(v)
+ * X = P is included (u = W/2, v = 0: pixel (ceil(W/2), 0)).
+ *
+ *   counts  : int32[m][W][W] output (row k, column l)
+ *   support : int64[m] output, pairs counted per image
+ *   max_d2  : float[m] output (may be NULL): the largest fl32 |d|^2 of a
+ *             counted pair, 0 when none (bounds the radius a culling grid needs)
+ * Returns 0, OR_EINVAL, or OR_EZERONORMAL.
+ */
+static int unit_normal_fp32(const float *normals, int64_t k, float nu[3])
+{
+    float x = normals[3 * k], y = normals[3 * k + 1], z = normals[3 * k + 2];
+    float l2 = fmaf(z, z, fmaf(y, y, x * x));
+    if (!(l2 > 0.0f) || !isfinite(l2)) return 0;
+    float inv = 1.0f / sqrtf(l2);
+    nu[0] = x * inv;
+    nu[1] = y * inv;
+    nu[2] = z * inv;
+    return 1;
+}
+
+int oracle_spin_images_nearest(const float *points, const float *normals, int64_t n,
+                               const int32_t *query_idx, int64_t m, int32_t W,
+                               float bin_size, float cos_s, int32_t *counts,
+                               int64_t *support, float *max_d2)
+{
+    int rc = check_common(points, normals, n, W, bin_size);
+    if (rc) return rc;
+    if (m < 0 || (m > 0 && (!counts || !support))) return OR_EINVAL;
+    if (!(cos_s >= -1.0f && cos_s <= 1.0f)) return OR_EINVAL;
+    const float half_w = 0.5f * (float)W;
+    const float top = (float)(W - 1);
+    const size_t npix = (size_t)W * (size_t)W;
+
+    for (int64_t q = 0; q < m; ++q) {
+        int64_t pi = query_idx ? (int64_t)query_idx[q] : q;
+        if (pi < 0 || pi >= n) return OR_EINVAL;
+        int32_t *C = counts + (size_t)q * npix;
+        memset(C, 0, npix * sizeof(int32_t));
+        float np[3];
+        if (!unit_normal_fp32(normals, pi, np)) return OR_EZERONORMAL;
+        const float px = points[3 * pi], py = points[3 * pi + 1], pz = points[3 * pi + 2];
+        int64_t cnt = 0;
+        float dmax = 0.0f;
+        for (int64_t j = 0; j < n; ++j) {
+            float nx[3];
+            if (!unit_normal_fp32(normals, j, nx)) return OR_EZERONORMAL;
+            const float dx = points[3 * j] - px;
+            const float dy = points[3 * j + 1] - py;
+            const float dz = points[3 * j + 2] - pz;
+            const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float ca = fmaf(np[2], nx[2], fmaf(np[1], nx[1], np[0] * nx[0]));
+            if (!(ca >= cos_s)) continue;
+            const float beta = fmaf(np[2], dz, fmaf(np[1], dy, np[0] * dx));
+            const float a2 = fmaf(-beta, beta, d2);
+            const float alpha = sqrtf(a2 > 0.0f ? a2 : 0.0f);
+            const float u = half_w - beta / bin_size;
+            const float v = alpha / bin_size;
+            const float k = ceilf(u), l = ceilf(v);
+            if (!(k >= 0.0f && k <= top && l >= 0.0f && l <= top)) continue;
+            C[(size_t)k * W + (size_t)l] += 1;
+            ++cnt;
+            if (d2 > dmax) dmax = d2;
+        }
+        support[q] = cnt;
+        if (max_d2) max_d2[q] = dmax;
+    }
+    return OR_OK;
+}
