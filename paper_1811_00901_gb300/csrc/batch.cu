@@ -117,6 +117,8 @@ struct Plan {
     size_t max_img_words = 4, smem = 0;
     int workers = 0;
     int modes = 0;  // tile-ring disciplines of the items' group shapes
+    int slow_workers = 0;
+    float slowdown = 1.0f;
     bool all_static = true;
     int nsteps = 0;
     std::vector<Piece> pieces;
@@ -171,6 +173,9 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
         set_error("too many image groups in one call");
         return SI_ERR_INVALID;
     }
+    // heterogeneity emulation: from the override, or the first item's rule
+    p->slow_workers = scheds[0].slow_workers;
+    p->slowdown = scheds[0].slowdown >= 1.0f ? scheds[0].slowdown : 1.0f;
     p->modes = 0;
     for (int k = 0; k < nitems; ++k) p->modes |= ring_mode(p->log2S[k]);
     p->modes = launch_modes(p->modes, probe);
@@ -431,6 +436,10 @@ si_status record_batch(const Plan &p, const std::vector<si_batch_item> &items, c
     a.img_words = (int)p.max_img_words;
     a.probe = probe ? 1 : 0;
     a.modes = p.modes;
+    // heterogeneity emulation: at most every launched block is slow
+    const int blocks = p.all_static ? p.nsteps : p.workers;
+    a.slow_workers = std::min(p.slow_workers, blocks);
+    a.slowdown = p.slowdown;
     launch_spin_kernel(a, p.all_static ? p.nsteps : p.workers, p.smem, stream);
     ++nk;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "spin kernel launch");

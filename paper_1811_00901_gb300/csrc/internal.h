@@ -54,6 +54,7 @@ constexpr int kStages = SI_STAGES;  // tile ring depth
 constexpr int kMaxRows = 512;       // stencil rows held in shared memory at once
 constexpr int kMaxW = 128;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // bounded device waits: 2 s
+constexpr uint64_t kSlowIdleCapNs = 1000000000ull;  // heterogeneity emulation: idle at most 1 s per step
 
 // Device flags (per mesh).
 constexpr unsigned kFlagOverflow = 1u;
@@ -150,6 +151,8 @@ struct LaunchArgs {
     int nitems;
     int img_words;          // shared words reserved for images (max over items)
     int probe;
+    int slow_workers = 0;   // heterogeneity emulation: blocks 0..slow_workers-1 are slow and request first
+    float slowdown = 1.0f;  // a slow block idles (slowdown - 1) x each step's time
     int modes = 0;          // tile-ring disciplines present (kModeBarrier | kModeProducer); 0 = both
 };
 

@@ -70,6 +70,7 @@ struct __align__(16) Header {
     int abort_flag;
     int slot_cnt[32];         // sliced groups: contributing pairs per image of this slice
     int cur_r, cur_o;          // barrier mode: producer row cursor
+    unsigned long long t_step;  // heterogeneity emulation: start of a slow block's step
 };
 
 constexpr int kHeaderBytes = (sizeof(Header) + 127) / 128 * 128;
@@ -714,6 +715,9 @@ __global__ void __launch_bounds__(kThreads, min_blocks_for<MODES>()) spin_kernel
     uint32_t phase_bits = 0;  // expected parity per stage (every thread tracks it)
     bool alive = true;
     int claim_iter = 0;
+    // heterogeneity emulation: slow blocks (index < a.slow_workers) take the
+    // first steps, one each, and the shared counter hands out the steps after
+    // them; H.t_step holds the start of a slow block's current step
 
     while (alive) {
         __syncthreads();
@@ -721,9 +725,12 @@ __global__ void __launch_bounds__(kThreads, min_blocks_for<MODES>()) spin_kernel
             int s;
             if (a.is_static)
                 s = claim_iter == 0 ? (int)blockIdx.x : a.nsteps;
+            else if ((int)blockIdx.x < a.slow_workers && claim_iter == 0)
+                s = (int)blockIdx.x;
             else
-                s = (int)atomicAdd(&a.ctr->step, 1ull);
+                s = a.slow_workers + (int)atomicAdd(&a.ctr->step, 1ull);
             H.claim = s;
+            if ((int)blockIdx.x < a.slow_workers) H.t_step = global_ns();
         }
         __syncthreads();
         const int step = H.claim;
@@ -769,6 +776,15 @@ __global__ void __launch_bounds__(kThreads, min_blocks_for<MODES>()) spin_kernel
                     }
                 }
             }
+        }
+        if ((int)blockIdx.x < a.slow_workers && alive && tid == 0) {
+            // a slow worker idles (slowdown - 1) x the time of its step, at most
+            // kSlowIdleCapNs; the other threads wait at the next claim's barrier
+            const uint64_t took = global_ns() - H.t_step;
+            uint64_t idle = (uint64_t)((double)took * (double)(a.slowdown - 1.0f));
+            if (idle > kSlowIdleCapNs) idle = kSlowIdleCapNs;
+            const uint64_t until = global_ns() + idle;
+            while (global_ns() < until) __nanosleep(2000);
         }
     }
     // ---- the last block to finish resets the dynamic step counter for the next launch
