@@ -248,6 +248,11 @@ si_status si_schedule_chunks(const si_schedule *schedule, int64_t units, int32_t
  * grid examines exactly { X : fl32(|X-P|^2) <= Rc2 } after culling. */
 float si_candidate_rc2(int32_t W, float bin_size);
 
+/* si_candidate_rc2 of a binning: SI_BIN_BILINEAR as above; SI_BIN_NEAREST
+ * with R^2 = ((W/2 + 1) B)^2 + ((W-1)B)^2 (a counted pair has -1 < u <= W-1,
+ * i.e. |beta| < (W/2 + 1) B, and alpha <= (W-1) B). */
+float si_candidate_rc2_binned(int32_t W, float bin_size, int32_t binning);
+
 /* ----------------------------------------------------------------- stats -- */
 /* Synchronises the device and reads the mesh's flags.  Returns
  * SI_ERR_OVERFLOW, SI_ERR_TIMEOUT or SI_ERR_INVALID (bad query index) when the

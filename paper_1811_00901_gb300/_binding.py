@@ -75,6 +75,7 @@ _SIGNATURES = {
                             ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)],
                            ctypes.c_int),
     "si_candidate_rc2": ([ctypes.c_int32, ctypes.c_float], ctypes.c_float),
+    "si_candidate_rc2_binned": ([ctypes.c_int32, ctypes.c_float, ctypes.c_int32], ctypes.c_float),
     "si_get_stats": ([_P, ctypes.POINTER(si_stats)], ctypes.c_int),
     "si_reset_stats": ([_P], ctypes.c_int),
     "si_set_timing": ([ctypes.c_int32], None),
@@ -241,6 +242,12 @@ def si_schedule_chunks(schedule, units, workers):
 
 def si_candidate_rc2(W, bin_size):
     return load().si_candidate_rc2(int(W), float(bin_size))
+
+
+def si_candidate_rc2_binned(W, bin_size, binning):
+    if isinstance(binning, str):
+        binning = BIN_NAMES[binning.upper()]
+    return load().si_candidate_rc2_binned(int(W), float(bin_size), int(binning))
 
 
 def si_get_stats(mesh, raise_on_flags=True):

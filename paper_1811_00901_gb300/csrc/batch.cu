@@ -87,7 +87,8 @@ __global__ void split_check_kernel(const ItemDesc *__restrict__ items, const int
         for (int p = lane; p < npix; p += 32) s += img[p];
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
-        if (lane == 0 && s != 65536ll * it.counts[q]) atomicOr(it.flags, kFlagOverflow);
+        const long long w = it.binning == SI_BIN_NEAREST ? 1ll : 65536ll;  // weight of one pair
+        if (lane == 0 && s != w * it.counts[q]) atomicOr(it.flags, kFlagOverflow);
     }
 }
 
@@ -119,6 +120,7 @@ struct Plan {
     int modes = 0;  // tile-ring disciplines of the items' group shapes
     int slow_workers = 0;
     float slowdown = 1.0f;
+    std::vector<int> binning;  // per item: si_binning
     bool all_static = true;
     int nsteps = 0;
     std::vector<Piece> pieces;
@@ -176,8 +178,12 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
     // heterogeneity emulation: from the override, or the first item's rule
     p->slow_workers = scheds[0].slow_workers;
     p->slowdown = scheds[0].slowdown >= 1.0f ? scheds[0].slowdown : 1.0f;
+    p->binning.resize(nitems);
     p->modes = 0;
-    for (int k = 0; k < nitems; ++k) p->modes |= ring_mode(p->log2S[k]);
+    for (int k = 0; k < nitems; ++k) {
+        p->binning[k] = scheds[k].binning;
+        p->modes |= ring_mode(p->log2S[k]) | (scheds[k].binning == SI_BIN_NEAREST ? kModeNearest : 0);
+    }
     p->modes = launch_modes(p->modes, probe);
     p->smem = 0;
     for (int k = 0; k < nitems; ++k)
@@ -347,7 +353,9 @@ void fill_blob(const Plan &p, const std::vector<si_batch_item> &items, const std
             d.perm = d_perm + p.sitems[p.sort_of[k]].qbase;
             d.perm_is_grid = 0;
         }
-        const float rc2 = si_candidate_rc2(it.W, it.bin_size);
+        const float rc2 = candidate_rc2(it.W, it.bin_size, p.binning[k]);
+        d.binning = p.binning[k];
+        d.B = it.bin_size;
         d.Rc2 = rc2;
         d.Rc = std::sqrt(rc2);
         d.cosS = it.cos_support_angle;

@@ -128,6 +128,8 @@ struct ItemDesc {
     // partial images into a zeroed `out` and per-image pair counts into `counts`
     int slices;
     int *counts;  // [m], zeroed, when slices > 1
+    int binning;  // si_binning: SI_BIN_NEAREST counts 1 per pair at (ceil(u), ceil(v))
+    float B;      // bin size (the nearest-bin count divides by it)
 };
 
 // A piece of the scheduled loop: units [u0, u1) of item `item`.
@@ -159,12 +161,14 @@ struct LaunchArgs {
 // Tile-ring discipline of a group shape: groups of <= 4 images run a producer
 // warp, larger groups a block barrier per tile.
 constexpr int kModeBarrier = 1, kModeProducer = 2;
+constexpr int kModeNearest = 4;  // some group uses the nearest-bin count (runtime-shape path)
 inline int ring_mode(int log2S) { return log2S <= 2 ? kModeProducer : kModeBarrier; }
 // Disciplines compiled into the kernel instance that runs a launch whose
 // groups use `modes`: one discipline alone gets its own instance; mixed
 // launches and probe launches run the instance with both.
 inline int launch_modes(int modes, bool probe) {
-    return !probe && (modes == kModeBarrier || modes == kModeProducer) ? modes : kModeBarrier | kModeProducer;
+    if (probe || (modes & kModeNearest)) return kModeBarrier | kModeProducer | kModeNearest;
+    return modes == kModeBarrier || modes == kModeProducer ? modes : kModeBarrier | kModeProducer;
 }
 
 // ---------------------------------------------------------- host helpers --
@@ -175,6 +179,9 @@ inline float support_alpha2(int W, float B) {
 }
 
 Grid *mesh_grid(Mesh *m, float cell, cudaStream_t stream, si_status *st);
+// Candidate threshold of a binning: fl32(R^2 (1 + 1e-5)) with R^2 = h^2 +
+// ((W-1)B)^2 (bilinear, h = W B / 2) or ((W/2 + 1) B)^2 + ((W-1)B)^2 (nearest).
+float candidate_rc2(int W, float bin_size, int binning);
 float grid_cell_for(const Mesh *m, int W, float bin, int grid_div);
 int choose_log2_group(int W, int requested_group);
 size_t image_words(int W, int log2S);

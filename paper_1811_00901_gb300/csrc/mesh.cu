@@ -25,15 +25,17 @@ __global__ void mesh_ingest_kernel(const float *__restrict__ pts, const float *_
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
         float a = nrm[3 * i], b = nrm[3 * i + 1], c = nrm[3 * i + 2];
-        float l2 = a * a + b * b + c * c;
+        // unit normal in IEEE FP32, each rounding spelled out (the nearest-bin
+        // count's pixel indices depend on these exact values)
+        float l2 = __fmaf_rn(c, c, __fmaf_rn(b, b, __fmul_rn(a, a)));
         bool ok = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(l2) && l2 > 0.0f;
         if (!ok) {
             my_bad = 1;
             l2 = 1.0f;
         }
-        float inv = 1.0f / sqrtf(l2);
+        float inv = __fdiv_rn(1.0f, __fsqrt_rn(l2));
         pos[i] = make_float4(x, y, z, 0.0f);
-        nrm_out[i] = make_float4(a * inv, b * inv, c * inv, 0.0f);
+        nrm_out[i] = make_float4(__fmul_rn(a, inv), __fmul_rn(b, inv), __fmul_rn(c, inv), 0.0f);
         lo[0] = fminf(lo[0], x);
         lo[1] = fminf(lo[1], y);
         lo[2] = fminf(lo[2], z);
@@ -140,6 +142,17 @@ bool is_device_pointer(const void *p) {
 
 // Cell edge for a call: the candidate radius divided by grid_div, rounded down
 // to a quarter octave so that calls with nearby (W, B) share one grid.
+// A contributing pair has |beta| <= h and alpha < (W-1) B (bilinear: all four
+// corners inside), or |beta| < (W/2 + 1) B and alpha <= (W-1) B (nearest bin:
+// -1 < u <= W-1); the 1e-5 inflation keeps FP32 rounding of |X-P|^2 from
+// dropping such a pair.
+float candidate_rc2(int W, float bin_size, int binning) {
+    const double B = (double)bin_size;
+    const double h = binning == SI_BIN_NEAREST ? ((double)W / 2.0 + 1.0) * B : (double)W * B / 2.0;
+    const double r = (double)(W - 1) * B;
+    return (float)((h * h + r * r) * (1.0 + 1e-5));
+}
+
 float grid_cell_for(const Mesh *m, int W, float bin, int grid_div) {
     (void)m;
     double R = std::sqrt((double)si_candidate_rc2(W, bin));
@@ -348,11 +361,10 @@ si_status si_mesh_destroy(si_mesh_t mesh) {
     return SI_OK;
 }
 
-float si_candidate_rc2(int32_t W, float bin_size) {
-    double B = (double)bin_size;
-    double h = (double)W * B / 2.0;
-    double r = (double)(W - 1) * B;
-    return (float)((h * h + r * r) * (1.0 + 1e-5));
+float si_candidate_rc2(int32_t W, float bin_size) { return si::candidate_rc2(W, bin_size, SI_BIN_BILINEAR); }
+
+float si_candidate_rc2_binned(int32_t W, float bin_size, int32_t binning) {
+    return si::candidate_rc2(W, bin_size, binning);
 }
 
 }  // extern "C"

@@ -140,7 +140,7 @@ __device__ int block_scan_rows(const int *len, int *off, int nr, Header &H) {
 
 // Constants of one item that the pair evaluation needs.
 struct PairConsts {
-    float Rc2, cosS, invB, halfW, umax, amax2;
+    float Rc2, cosS, invB, halfW, umax, amax2, B;
 };
 
 // Shape of a group's images: compile-time when WT > 0, else runtime.
@@ -213,8 +213,34 @@ __device__ __forceinline__ void eval_pair(const PairDist &pd, const float4 NX, c
     }
 }
 
-// One warp trip: two candidates per lane, at p0 and p1 (position, normal).
+// Algorithm 1's own count (SI_BIN_NEAREST): pixel (ceil(u), ceil(v)) += 1 for
+// 0 <= ceil(u), ceil(v) <= W-1, in IEEE FP32 with every rounding spelled out
+// (the pixel index is decided by the rounded value):
+//   angle n.n_X = fma(n.z, nX.z, fma(n.y, nX.y, n.x*nX.x)) >= cos S
+//   beta = fma(n.z, dz, fma(n.y, dy, n.x*dx)); alpha = sqrt(max(fma(-beta, beta, |d|^2), 0))
+//   u = W/2 - beta/B, v = alpha/B (correctly rounded divisions and square root).
+// `img_q` is the slot's pixel (0, 0).
 template <int WT, int LS, bool PROBE>
+__device__ __forceinline__ void eval_pair_nearest(const PairDist &pd, const float4 NX, const bool live,
+                                                  const float4 N, const PairConsts &k, const Shape<WT, LS> sh,
+                                                  int *img_q, int &cnt, int *pc_s) {
+    const float ca = __fmaf_rn(N.z, NX.z, __fmaf_rn(N.y, NX.y, __fmul_rn(N.x, NX.x)));
+    const float beta = __fmaf_rn(N.z, pd.dz, __fmaf_rn(N.y, pd.dy, __fmul_rn(N.x, pd.dx)));
+    const float a2 = __fmaf_rn(-beta, beta, pd.d2);
+    const float alpha = __fsqrt_rn(a2 > 0.0f ? a2 : 0.0f);
+    const float u = __fsub_rn(k.halfW, __fdiv_rn(beta, k.B));
+    const float v = __fdiv_rn(alpha, k.B);
+    const float kr = ceilf(u), lc = ceilf(v);
+    const bool in = live & (ca >= k.cosS) & (kr >= 0.0f) & (kr <= k.umax) & (lc >= 0.0f) & (lc <= k.umax);
+    if (PROBE && in) atomicAdd(pc_s, 1);
+    if (in) {
+        atomicAdd(img_q + (int)kr * sh.row_words() + ((int)lc << sh.log2S()), 1);
+        ++cnt;
+    }
+}
+
+// One warp trip: two candidates per lane, at p0 and p1 (position, normal).
+template <int WT, int LS, bool PROBE, bool NB>
 __device__ __forceinline__ void trip(const float4 *p0, const float4 *p1, const bool l0, const bool l1,
                                      const float4 P, const float4 N, const PairConsts &k, const Shape<WT, LS> sh,
                                      int *img_adj, int &cnt, int *pc_c, int *pc_s, unsigned *pc_h) {
@@ -232,8 +258,14 @@ __device__ __forceinline__ void trip(const float4 *p0, const float4 *p1, const b
         }
     }
     const float4 N0 = p0[1], N1 = p1[1];
-    eval_pair<WT, LS, PROBE>(d0, N0, near0, N, k, sh, img_adj, cnt, pc_s);
-    eval_pair<WT, LS, PROBE>(d1, N1, near1, N, k, sh, img_adj, cnt, pc_s);
+    if constexpr (NB) {
+        // img_adj is the slot's pixel (0, 0) for the nearest-bin count
+        eval_pair_nearest<WT, LS, PROBE>(d0, N0, near0, N, k, sh, img_adj, cnt, pc_s);
+        eval_pair_nearest<WT, LS, PROBE>(d1, N1, near1, N, k, sh, img_adj, cnt, pc_s);
+    } else {
+        eval_pair<WT, LS, PROBE>(d0, N0, near0, N, k, sh, img_adj, cnt, pc_s);
+        eval_pair<WT, LS, PROBE>(d1, N1, near1, N, k, sh, img_adj, cnt, pc_s);
+    }
 }
 
 // Whether a full tile (kTile candidates) of this shape takes a path without
@@ -250,7 +282,7 @@ constexpr bool has_full_path() {
 //    w*cpw + 2*NCONS*cpw*t (a compile-time count, unrolled);
 //  * NCONS consumer warps: trip t covers candidates [2*cpw*t, 2*cpw*(t+1)),
 //    dealt round-robin.
-template <int WT, int LS, bool PROBE, int NCONS, int TN, bool FULL>
+template <int WT, int LS, bool PROBE, bool NB, int NCONS, int TN, bool FULL>
 __device__ __forceinline__ void consume_tile(const float4 *__restrict__ tile, const int len, const int warp,
                                              const int lane, const bool active, const float4 P, const float4 N,
                                              const PairConsts &k, const Shape<WT, LS> sh, int *img_adj, int &cnt,
@@ -265,40 +297,40 @@ __device__ __forceinline__ void consume_tile(const float4 *__restrict__ tile, co
         const float4 *t0 = tile + 2 * (warp * cpw + sub);
 #pragma unroll 4
         for (int tr = 0; tr < kTrips; ++tr)
-            trip<WT, LS, PROBE>(t0 + 4 * tr * kStride, t0 + 4 * tr * kStride + 2 * kStride, active, active, P, N,
+            trip<WT, LS, PROBE, NB>(t0 + 4 * tr * kStride, t0 + 4 * tr * kStride + 2 * kStride, active, active, P, N,
                                 k, sh, img_adj, cnt, pc_c, pc_s, pc_h);
     } else if constexpr (FULL) {
         constexpr int kCpw = 32 >> LS;
         constexpr int kTrips = TN / (2 * kCpw);
         const float4 *t0 = tile + 2 * sub;
         for (int tr = warp; tr < kTrips; tr += NCONS)
-            trip<WT, LS, PROBE>(t0 + 4 * tr * kCpw, t0 + 4 * tr * kCpw + 2 * kCpw, active, active, P, N, k, sh,
+            trip<WT, LS, PROBE, NB>(t0 + 4 * tr * kCpw, t0 + 4 * tr * kCpw + 2 * kCpw, active, active, P, N, k, sh,
                                 img_adj, cnt, pc_c, pc_s, pc_h);
     } else {
         for (int cb = warp * cpw; cb < len; cb += 2 * stride) {
             const int c0 = cb + sub, c1 = cb + stride + sub;
             const bool l0 = active & (c0 < len), l1 = active & (c1 < len);
             const int i0 = l0 ? c0 : 0, i1 = l1 ? c1 : 0;
-            trip<WT, LS, PROBE>(tile + 2 * i0, tile + 2 * i1, l0, l1, P, N, k, sh, img_adj, cnt, pc_c, pc_s, pc_h);
+            trip<WT, LS, PROBE, NB>(tile + 2 * i0, tile + 2 * i1, l0, l1, P, N, k, sh, img_adj, cnt, pc_c, pc_s, pc_h);
         }
     }
 }
 
 // Consumes a tile, through the range-check-free path when it holds TN
 // candidates (TN = 0: shapes known only at run time, no such path).
-template <int WT, int LS, bool PROBE, int NCONS, int TN>
+template <int WT, int LS, bool PROBE, bool NB, int NCONS, int TN>
 __device__ __forceinline__ void consume_any(const float4 *__restrict__ tile, const int len, const int warp,
                                             const int lane, const bool active, const float4 P, const float4 N,
                                             const PairConsts &k, const Shape<WT, LS> sh, int *img_adj, int &cnt,
                                             int *pc_c, int *pc_s, unsigned *pc_h) {
     if constexpr (has_full_path<WT, LS, NCONS, TN>()) {
         if (len == TN) {
-            consume_tile<WT, LS, PROBE, NCONS, TN, true>(tile, len, warp, lane, active, P, N, k, sh, img_adj, cnt, pc_c,
+            consume_tile<WT, LS, PROBE, NB, NCONS, TN, true>(tile, len, warp, lane, active, P, N, k, sh, img_adj, cnt, pc_c,
                                                      pc_s, pc_h);
             return;
         }
     }
-    consume_tile<WT, LS, PROBE, NCONS, TN, false>(tile, len, warp, lane, active, P, N, k, sh, img_adj, cnt, pc_c, pc_s,
+    consume_tile<WT, LS, PROBE, NB, NCONS, TN, false>(tile, len, warp, lane, active, P, N, k, sh, img_adj, cnt, pc_c, pc_s,
                                               pc_h);
 }
 
@@ -330,7 +362,7 @@ __device__ __forceinline__ void row_cursor(const int *row_off, int nr, int first
 // Generates the images of one unit u of item `it` (a group, or one slice of
 // a group's candidate stream).  Returns false when a bounded wait gave up
 // (the block then stops).
-template <int WT, int LS, bool PROBE, bool PMODE>
+template <int WT, int LS, bool PROBE, bool PMODE, bool NB = false>
 __device__ bool process_group(const ItemDesc &it, const int u, const int step, const SmemView &sv,
                               uint32_t &phase_bits) {
     Header &H = *sv.H;
@@ -344,7 +376,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
     const float ox = it.origin[0], oy = it.origin[1], oz = it.origin[2];
     const float cell = it.cell, inv = it.inv_cell, margin = it.margin;
     const int dx_ = it.dims[0], dy_ = it.dims[1], dz_ = it.dims[2];
-    const PairConsts k{it.Rc2, it.cosS, it.invB, it.halfW, it.umax, it.amax2};
+    const PairConsts k{it.Rc2, it.cosS, it.invB, it.halfW, it.umax, it.amax2, it.B};
     const float Rc = it.Rc;
     const int slot = lane & (S - 1);
     // candidates per tile: a compile-time constant for the specialised shapes
@@ -435,7 +467,9 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
     const float4 qN = Q[slot].n;
     const bool active = slot < nq;
     int cnt = 0;
-    int *img_adj = img + slot - kMagicHi * (sh.row_words() + S);
+    // bilinear: pixel (0, 0) of the slot moved back by the coordinates' exponent
+    // bias; nearest bin: pixel (0, 0) itself
+    int *img_adj = NB ? img + slot : img + slot - kMagicHi * (sh.row_words() + S);
     const int ylo = H.ylo, zlo = H.zlo;
     const int ny = H.yhi - ylo + 1, nz = H.zhi - zlo + 1;
     const int nrows_total = ny * nz;
@@ -538,7 +572,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
                 phase_bits ^= 1u << b;
                 const int len = min(TN, total - t * TN);
                 if (PROBE && tid < nq) sv.pc_examined[tid] += len;
-                consume_any<WT, LS, PROBE, kProdConsumers, TNC>(sv.tiles + (size_t)b * TN * 2, len, warp, lane,
+                consume_any<WT, LS, PROBE, NB, kProdConsumers, TNC>(sv.tiles + (size_t)b * TN * 2, len, warp, lane,
                                                            active, qP, qN, k, sh, img_adj, cnt, sv.pc_culled + slot,
                                                            sv.pc_support + slot, sv.pc_hash + slot);
                 __syncwarp();
@@ -592,7 +626,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
                 phase_bits ^= 1u << b;
                 const int len = min(TN, total - (tlo + tt) * TN);
                 if (PROBE && tid < nq) sv.pc_examined[tid] += len;
-                consume_any<WT, LS, PROBE, kWarps, TNC>(sv.tiles + (size_t)b * TN * 2, len, warp, lane, active, qP,
+                consume_any<WT, LS, PROBE, NB, kWarps, TNC>(sv.tiles + (size_t)b * TN * 2, len, warp, lane, active, qP,
                                                    qN, k, sh, img_adj, cnt, sv.pc_culled + slot, sv.pc_support + slot,
                                                    sv.pc_hash + slot);
             }
@@ -649,7 +683,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
     }
     if (lane == 0) {
         atomicAdd(&H.grp_pix, (unsigned long long)pix);
-        atomicAdd(&H.grp_weight, (unsigned long long)cnt * 65536ull);
+        atomicAdd(&H.grp_weight, (unsigned long long)cnt * (NB ? 1ull : 65536ull));
     }
     if (PROBE && tid < nq && Q[tid].slot >= 0) {
         const int q = Q[tid].slot;
@@ -669,7 +703,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
     return true;
 }
 
-// MODES: the tile-ring disciplines compiled in (kModeBarrier | kModeProducer);
+// MODES: the paths compiled in (kModeBarrier | kModeProducer | kModeNearest);
 // a launch whose groups all use one discipline runs the instance without the
 // other, whose registers are then allocated for its own loop alone.  Groups
 // in producer mode hold >= 67 KB of images, so at most two blocks fit on an
@@ -742,8 +776,14 @@ __global__ void __launch_bounds__(kThreads, min_blocks_for<MODES>()) spin_kernel
             const ItemDesc &it = a.items[pc.item];
             const int key = it.W * 8 + it.log2S;
             for (int u = pc.u0; u < pc.u1 && alive; ++u) {
-                // specialised shapes for the common widths, a runtime one otherwise
-                if (it.log2S <= 2) {
+                // specialised shapes for the common widths, a runtime one otherwise;
+                // the nearest-bin count runs on the runtime shape
+                if ((MODES & kModeNearest) != 0 && it.binning == SI_BIN_NEAREST) {
+                    if constexpr ((MODES & kModeNearest) != 0) {
+                        alive = it.log2S <= 2 ? process_group<0, 0, PROBE, true, true>(it, u, step, sv, phase_bits)
+                                              : process_group<0, 0, PROBE, false, true>(it, u, step, sv, phase_bits);
+                    }
+                } else if (it.log2S <= 2) {
                     if constexpr ((MODES & kModeProducer) != 0) {
                         switch (key) {
                             case 64 * 8 + 1:
@@ -808,6 +848,8 @@ size_t image_words(int W, int log2S) {
 
 size_t spin_smem_bytes(int W, int log2S) { return (size_t)shape_smem(W, log2S, tile_for_shape(W, log2S)); }
 
+constexpr int kModeAll = kModeBarrier | kModeProducer | kModeNearest;
+
 cudaError_t setup_spin_kernel_attributes(size_t smem_bytes) {
     static size_t done = 0;
     if (smem_bytes <= done) return cudaSuccess;
@@ -816,7 +858,8 @@ cudaError_t setup_spin_kernel_attributes(size_t smem_bytes) {
     cudaError_t e = cudaFuncSetAttribute(spin_kernel<false, kModeBarrier | kModeProducer>, attr, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(spin_kernel<false, kModeBarrier>, attr, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(spin_kernel<false, kModeProducer>, attr, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(spin_kernel<true, kModeBarrier | kModeProducer>, attr, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(spin_kernel<false, kModeAll>, attr, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(spin_kernel<true, kModeAll>, attr, bytes);
     if (e == cudaSuccess) done = smem_bytes;
     return e;
 }
@@ -830,22 +873,26 @@ int blocks_per_sm_for(size_t smem_bytes, int modes) {
     else if (modes == kModeProducer)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spin_kernel<false, kModeProducer>, kThreads,
                                                           smem_bytes);
-    else
+    else if (modes == (kModeBarrier | kModeProducer))
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spin_kernel<false, kModeBarrier | kModeProducer>,
                                                           kThreads, smem_bytes);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spin_kernel<false, kModeAll>, kThreads, smem_bytes);
     return e == cudaSuccess ? n : 0;
 }
 
 void launch_spin_kernel(const LaunchArgs &a, int blocks, size_t smem, cudaStream_t stream) {
     // a.modes is launch_modes(...) of the call
     if (a.probe)
-        spin_kernel<true, kModeBarrier | kModeProducer><<<blocks, kThreads, smem, stream>>>(a);
+        spin_kernel<true, kModeAll><<<blocks, kThreads, smem, stream>>>(a);
     else if (a.modes == kModeBarrier)
         spin_kernel<false, kModeBarrier><<<blocks, kThreads, smem, stream>>>(a);
     else if (a.modes == kModeProducer)
         spin_kernel<false, kModeProducer><<<blocks, kThreads, smem, stream>>>(a);
-    else
+    else if (a.modes == (kModeBarrier | kModeProducer))
         spin_kernel<false, kModeBarrier | kModeProducer><<<blocks, kThreads, smem, stream>>>(a);
+    else
+        spin_kernel<false, kModeAll><<<blocks, kThreads, smem, stream>>>(a);
 }
 
 // Largest group (power of two, <= 32, or the requested one) whose images fit

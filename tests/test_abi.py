@@ -75,6 +75,19 @@ def test_candidate_threshold_matches_oracle(lib):
         assert spin.si_candidate_rc2(W, B) == oracle.candidate_rc2(W, B)
 
 
+def test_nearest_bin_threshold_covers_every_counted_pair(lib):
+    """The library culls the nearest-bin count at si_candidate_rc2_binned; the
+    oracle's counted pairs (all-pairs, no culling) must all lie within it."""
+    import oracle
+    import paper_1811_00901_gb300 as spin
+    from paper_1811_00901_gb300 import workloads as wl
+    pts, nrm = wl.heightfield(2500, 8)
+    for W, B in [(16, 0.05), (32, 0.01), (5, 0.1)]:
+        _, _, dmax = oracle.spin_images_nearest(pts, nrm, W, B, -1.0, query_idx=np.arange(0, 2500, 5).astype(np.int32))
+        assert float(dmax.max()) <= spin.si_candidate_rc2_binned(W, B, "NEAREST")
+        assert spin.si_candidate_rc2_binned(W, B, "BILINEAR") == spin.si_candidate_rc2(W, B)
+
+
 def test_invalid_chunk_table_args(lib):
     import ctypes
     n = ctypes.c_int64()
