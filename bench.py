@@ -143,6 +143,18 @@ def _measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def _group_cost_cov(examined_per_image):
+    """sigma / mu of the per-group cost.  A group's cost follows its candidate
+    stream, whose length every image of the group reports as its examined
+    count, so the spread over images is the spread over groups."""
+    e = np.asarray(examined_per_image, dtype=np.float64)
+    return float(e.std() / max(e.mean(), 1e-30))
+
+
+def sms_count(torch, dev):
+    return torch.cuda.get_device_properties(dev).multi_processor_count
+
+
 def _quartiles(xs):
     q = np.percentile(np.asarray(xs, dtype=np.float64), [25, 50, 75])
     return [float(v) for v in q]
@@ -242,6 +254,7 @@ def run_ours(args):
     n_culled = int(culled.sum().item())
     n_support = int(support.sum().item())
     n_examined = int(examined.sum().item())
+    examined_per_image = examined.cpu().numpy()
     # measured shared-atomic peak (denominator of the splat roofline)
     atom_peak = spin.si_peak_smem_atomics(0, stream)
     atom_spread = spin.si_peak_smem_atomics(1, stream)
@@ -372,6 +385,27 @@ def run_ours(args):
                                                 stream, kinds=("STATIC", "SS", "GSS", "FAC"))
         extra["scene-1M-W64"] = bench_single(spin, torch, dev, wl.large_scene(), ex_steps, args.warmup, flush,
                                              stream, kinds=("STATIC", "FAC"))
+        # probabilistic factoring with sigma / mu of the group cost measured by
+        # the probe run (a group's cost follows its candidate stream length)
+        cov = _group_cost_cov(examined_per_image)
+        extra["fac-prob-heightfield-100k-W32"] = dict(
+            bench_single(spin, torch, dev, c, ex_steps, args.warmup, flush, stream, scheds={
+                "FAC": spin.make_schedule("FAC", **shape),
+                "FAC_PROB": spin.make_schedule("FAC_PROB", fac_cov=cov, **shape)}), fac_cov=cov)
+        # heterogeneity emulation (Sec. 5.2's Type2 + Type1 runs): the first half
+        # of the workers 3x slower, and they request first
+        P = sms_count(torch, dev) * 3
+        het = {k: spin.make_schedule(k, num_workers=P, slow_workers=P // 2, slowdown=3.0, fac_cov=cov, **shape)
+               for k in ("STATIC", "SS", "GSS", "FAC", "FAC_PROB")}
+        h = bench_single(spin, torch, dev, c, ex_steps, args.warmup, flush, stream, scheds=het)
+        h["emulation"] = {"workers": P, "slow_workers": P // 2, "slowdown": 3.0, "slow_request_first": True}
+        h["over_static"] = {k: v["images_per_s"] / h["by_schedule"]["STATIC"]["images_per_s"]
+                            for k, v in h["by_schedule"].items()}
+        extra["heterogeneous-heightfield-100k-W32"] = h
+        # Algorithm 1's own nearest-bin count on the bench workload
+        extra["nearest-bin-heightfield-100k-W32"] = bench_single(
+            spin, torch, dev, c, ex_steps, args.warmup, flush, stream,
+            scheds={k: spin.make_schedule(k, binning="NEAREST") for k in ("STATIC", "FAC")})
         del out
         torch.cuda.empty_cache()
         extra["batched-512-spheres"] = bench_batched(spin, torch, dev, ex_steps, args.warmup, stream)
@@ -380,6 +414,7 @@ def run_ours(args):
         line["workloads"] = extra
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(c, budget_s=args.cpu_seconds)
+        line["cpu_dls_baseline"] = cpu_dls_baseline(c)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -391,16 +426,18 @@ def run_ours(args):
 # the other workloads (secondary keys of the same line)
 # --------------------------------------------------------------------------
 
-def bench_single(spin, torch, dev, c, steps, warmup, flush, stream, kinds=("STATIC", "FAC")):
-    """One mesh, all its images (or its query list), per rule; kernel time by events."""
+def bench_single(spin, torch, dev, c, steps, warmup, flush, stream, kinds=("STATIC", "FAC"), scheds=None):
+    """One mesh, all its images (or its query list), per rule; kernel time by
+    events.  ``scheds`` (name -> si_schedule) replaces ``kinds`` when given."""
     n, m, W, B, cs = c["points"].shape[0], c["m"], c["W"], float(c["bin_size"]), float(c["cos_s"])
     tp = torch.from_numpy(c["points"]).to(dev)
     tn = torch.from_numpy(c["normals"]).to(dev)
     tq = None if c["query_idx"] is None else torch.from_numpy(c["query_idx"]).to(dev)
     out = torch.empty((m, W, W), dtype=torch.int32, device=dev)
     res = {}
-    for kind in kinds:
-        sched = spin.make_schedule(kind)
+    if scheds is None:
+        scheds = {kind: spin.make_schedule(kind) for kind in kinds}
+    for kind, sched in scheds.items():
         times, kms = [], []
         for k in range(warmup + steps):
             flush.zero_()
@@ -564,6 +601,32 @@ def cpu_baseline(c, budget_s=12.0):
     return {"value": nq / t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d random images of the %s workload (all %d points each, FP64, single thread)" % (
                 nq, c["name"], c["points"].shape[0])}
+
+
+def cpu_dls_baseline(c, budget_s=3.0):
+    """The oracle's image loop under OpenMP schedule(static), (dynamic, 1) and
+    (guided) on all host cores: the shared-memory CPU analogue of PSIA-STATIC,
+    EPSIA-SS and EPSIA-GSS.  The first nq images, nq sized for ~budget_s each."""
+    import oracle
+    if not oracle.omp_available():
+        return {"unavailable": "the host compiler has no OpenMP"}
+    cores = oracle.omp_max_threads()
+    pts, nrm = c["points"], c["normals"]
+    W, B, cs = c["W"], c["bin_size"], c["cos_s"]
+    probe = np.arange(2 * cores, dtype=np.int32)
+    t0 = time.perf_counter()
+    oracle.spin_images_omp(pts, nrm, W, B, cs, query_idx=probe, rule="static")
+    per = (time.perf_counter() - t0) / len(probe)
+    nq = int(max(2 * cores, min(c["m"], budget_s / max(per, 1e-9))))
+    q = np.arange(nq, dtype=np.int32)
+    out = {"kind": "oracle, OpenMP image loop", "cores": cores, "unit": UNIT,
+           "sample": "images 0..%d of the %s workload (all %d points each, FP64)" % (nq - 1, c["name"],
+                                                                                    pts.shape[0])}
+    for rule, name in (("static", "static"), ("dynamic", "dynamic_1"), ("guided", "guided")):
+        t0 = time.perf_counter()
+        oracle.spin_images_omp(pts, nrm, W, B, cs, query_idx=q, rule=rule)
+        out[name] = nq / (time.perf_counter() - t0)
+    return out
 
 
 def run_reference(args):

@@ -151,6 +151,60 @@ def spin_images_nearest(points, normals, W, bin_size, cos_s, query_idx=None, m=N
     return cnt, sup, dmax
 
 
+_lib_omp = None
+OMP_RULES = {"static": 0, "dynamic": 1, "guided": 2}
+
+
+def _load_omp():
+    """The OpenMP image loop, or None when the host compiler has no OpenMP."""
+    global _lib_omp
+    if _lib_omp is not None:
+        return _lib_omp or None
+    from .build import build_oracle_omp
+    path = build_oracle_omp()
+    if path is None:
+        _lib_omp = False
+        return None
+    lib = ctypes.CDLL(path)
+    f32p = ctypes.POINTER(ctypes.c_float)
+    lib.oracle_spin_images_omp.argtypes = [f32p, f32p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.c_int32, ctypes.c_int32]
+    lib.oracle_spin_images_omp.restype = ctypes.c_int
+    lib.oracle_omp_max_threads.restype = ctypes.c_int
+    _lib_omp = lib
+    return lib
+
+
+def omp_available():
+    return _load_omp() is not None
+
+
+def omp_max_threads():
+    lib = _load_omp()
+    return lib.oracle_omp_max_threads() if lib else 0
+
+
+def spin_images_omp(points, normals, W, bin_size, cos_s, query_idx=None, m=None, rule="static", threads=0):
+    """spin_images (without flags) with the image loop under OpenMP
+    schedule(static), schedule(dynamic, 1) or schedule(guided)."""
+    lib = _load_omp()
+    if lib is None:
+        raise RuntimeError("the host compiler has no OpenMP")
+    p, nr = _f32x3(points), _f32x3(normals)
+    n = p.shape[0]
+    q, m = _queries(query_idx, n if m is None else m)
+    img = np.zeros((m, W, W), dtype=np.float64)
+    sup = np.zeros(m, dtype=np.int64)
+    rc = lib.oracle_spin_images_omp(_ptr(p, ctypes.c_float), _ptr(nr, ctypes.c_float), n, _ptr(q, ctypes.c_int32),
+                                    m, int(W), float(bin_size), float(cos_s), _ptr(img, ctypes.c_double),
+                                    _ptr(sup, ctypes.c_int64), OMP_RULES[rule], int(threads))
+    if rc != 0:
+        raise ValueError("oracle_spin_images_omp failed with code %d" % rc)
+    return img, sup
+
+
 def support_radius2(W, bin_size):
     """R^2 = h^2 + ((W - 1) B)^2, h = W B / 2 (double)."""
     return _load().oracle_support_radius2(int(W), float(bin_size))

@@ -30,5 +30,31 @@ def build_oracle(force=False):
     return out
 
 
+SRC_OMP = os.path.join(HERE, "spin_oracle_omp.c")
+
+
+def library_path_omp():
+    return os.path.join(OUT_DIR, "liboracle_omp.so")
+
+
+def build_oracle_omp(force=False):
+    """The OpenMP image loop (CPU baseline).  Returns None when the host
+    compiler has no OpenMP; nothing else depends on it."""
+    out = library_path_omp()
+    if (not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(SRC_OMP)
+            and os.path.getmtime(out) >= os.path.getmtime(SRC)):
+        return out
+    os.makedirs(OUT_DIR, exist_ok=True)
+    tmp = out + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-fopenmp",
+           "-shared", "-o", tmp, SRC, SRC_OMP, "-lm"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        return None
+    os.replace(tmp, out)
+    return out
+
+
 if __name__ == "__main__":
     print(build_oracle(force=True))
+    print(build_oracle_omp(force=True))

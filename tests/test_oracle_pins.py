@@ -258,3 +258,16 @@ def test_invalid_arguments():
     with pytest.raises(ValueError):
         oracle.spin_images(pts, nrm, 4, float("nan"), 0.0)
     assert math.isfinite(oracle.support_radius2(4, 0.1))
+
+
+@pytest.mark.parametrize("rule", ["static", "dynamic", "guided"])
+def test_openmp_image_loop_equals_the_serial_oracle(rule):
+    """The CPU baseline's parallel image loop computes the same images."""
+    if not oracle.omp_available():
+        pytest.skip("no OpenMP in the host compiler")
+    pts, nrm = wl.heightfield(1500, 5)
+    q = np.arange(0, 1500, 11).astype(np.int32)
+    ref, sup, _ = oracle.spin_images(pts, nrm, 16, 0.02, 0.5, query_idx=q)
+    img, sup2 = oracle.spin_images_omp(pts, nrm, 16, 0.02, 0.5, query_idx=q, rule=rule, threads=4)
+    np.testing.assert_array_equal(img, ref)
+    np.testing.assert_array_equal(sup2, sup)
