@@ -188,18 +188,20 @@ __device__ __forceinline__ void eval_pair(const PairDist &pd, const float4 NX, c
     const float u = fmaf(-beta, k.invB, k.halfW);
     const bool in = live & (ca >= k.cosS) & (u >= 0.0f) & (u < k.umax) & (a2 < k.amax2);
     if (PROBE && in) atomicAdd(pc_s, 1);
-    // alpha / B through the approximate reciprocal square root; the support
+    // alpha through the approximate reciprocal square root; the support
     // decision above does not depend on it, and 16-bit quantisation absorbs
     // its last-bit error
     float r;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(fmaxf(a2, 1e-30f)));  // argument is normal
-    const float v = a2 * r * k.invB;
     // U = rn(u * 2^16): u * 2^16 is exact and below 2^23 (0 <= u < W - 1 <= 127
     // for a contributing pair), so adding 2^23 rounds it to an integer held in
     // the low 23 bits; the low 16 bits are the fraction, the top 16 the row
-    // plus kMagicHi
+    // plus kMagicHi.  V = rn(alpha * (2^16 / B)) the same way, capped at column
+    // W - 1 with a zero fraction: the column test bounds alpha, not the
+    // approximate v, which may exceed W - 1 by a few ulps
     const uint32_t Ub = __float_as_uint(fmaf(u, 65536.0f, 8388608.0f));
-    const uint32_t Vb = __float_as_uint(fmaf(v, 65536.0f, 8388608.0f));
+    const uint32_t Vb = min(__float_as_uint(fmaf(a2 * r, k.invB * 65536.0f, 8388608.0f)),
+                            0x4B000000u + ((uint32_t)k.umax << 16));
     const uint32_t A = Ub & 0xFFFFu, Bq = Vb & 0xFFFFu;
     const uint32_t w11 = (A * Bq + 32768u) >> 16;
     if (in) {
@@ -295,7 +297,7 @@ __device__ __forceinline__ void consume_tile(const float4 *__restrict__ tile, co
         constexpr int kStride = NCONS * (32 >> LS);
         constexpr int kTrips = TN / (2 * kStride);
         const float4 *t0 = tile + 2 * (warp * cpw + sub);
-#pragma unroll 4
+#pragma unroll
         for (int tr = 0; tr < kTrips; ++tr)
             trip<WT, LS, PROBE, NB>(t0 + 4 * tr * kStride, t0 + 4 * tr * kStride + 2 * kStride, active, active, P, N,
                                 k, sh, img_adj, cnt, pc_c, pc_s, pc_h);

@@ -316,3 +316,31 @@ def test_bad_query_index_is_reported_not_read():
     good = np.array([3, 7, 11], np.int32)
     ref, _ = gpu_run(pts, nrm, 16, 0.05, 0.5, query_idx=good)
     np.testing.assert_array_equal(o[[0, 2, 4]], ref)
+
+
+@pytest.mark.parametrize("W,B", [(32, 0.01), (128, 0.003), (16, 0.05)])
+def test_column_edge_pairs_keep_their_whole_weight(W, B):
+    """Pairs whose alpha lies within a few ulps of (W-1) B: the column test is
+    alpha^2 < ((W-1)B)^2, while v comes from an approximate reciprocal square
+    root, so v may land a hair above W-1.  Every contributing pair must still
+    put its whole weight 65536 inside the W x W image (the exact overflow check
+    would otherwise report a pixel overflow)."""
+    import paper_1811_00901_gb300 as spin
+    edge = np.float32((W - 1) * B)
+    ds = [edge]
+    for _ in range(300):
+        ds.append(np.nextafter(ds[-1], np.float32(0)))
+    up = edge
+    for _ in range(40):
+        up = np.nextafter(up, np.float32(1))
+        ds.append(up)
+    ds = np.array(ds, np.float32)
+    ang = np.linspace(0, 2 * np.pi, len(ds), endpoint=False)
+    pts = np.zeros((len(ds) + 1, 3), np.float32)
+    pts[1:, 0] = (ds * np.cos(ang)).astype(np.float32)
+    pts[1:, 1] = (ds * np.sin(ang)).astype(np.float32)
+    nrm = np.tile(np.array([[0, 0, 1]], np.float32), (len(pts), 1))
+    q = np.array([0], np.int32)
+    got, pr = gpu_run(pts, nrm, W, B, 0.0, query_idx=q, probe=True, schedule=spin.make_schedule("SS"))
+    assert got[0].astype(np.int64).sum() == 65536 * int(pr["support"][0])
+    compare_with_oracle(got, pts, nrm, W, B, 0.0, q, np.array([0]))
