@@ -196,10 +196,15 @@ si_status si_generate_batched(const si_batch_item *items, int32_t count,
                               const si_schedule *override_or_null, si_stream stream);
 
 /* si_generate_host -- the whole path from HOST buffers: copies points and
- * normals in, builds a temporary mesh, generates, copies the images out to
+ * normals in, builds a temporary mesh, generates, delivers the images to
  * host memory and synchronises `stream` before returning.
  *   points, normals : host float[n][3];  query_idx : host int32[m] or NULL;
- *   out             : host int32[m][W][W] (pinned memory copies fastest). */
+ *   out             : host int32[m][W][W].
+ * Delivery, for m >= 32768: page-locked `out` (mapped into the device's
+ * address space, as cudaHostAlloc memory is) is written by the kernel itself
+ * while it runs; pageable `out` is filled by downloads of query ranges that
+ * overlap the generation of the next range.  Smaller calls download once.
+ * Images are the same in every case. */
 si_status si_generate_host(const float *points, const float *normals, int64_t n,
                            const int32_t *query_idx, int64_t m, int32_t W, float bin_size,
                            float cos_support_angle, si_schedule schedule, int32_t *out,

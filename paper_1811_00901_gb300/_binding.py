@@ -207,7 +207,8 @@ def si_generate_batched(items, schedule=None, stream=None):
 
 
 def si_generate_host(points, normals, n, query_idx, m, W, bin_size, cos_s, schedule, out, stream=None):
-    """All buffers are host pointers / CPU tensors (pinned is fastest)."""
+    """All buffers are host pointers / CPU tensors (page-locked output is
+    written by the kernel directly)."""
     _check(load().si_generate_host(_ptr(points), _ptr(normals), int(n), _ptr(query_idx), int(m), int(W),
                                    float(bin_size), float(cos_s), schedule, _ptr(out), _stream_ptr(stream)))
 

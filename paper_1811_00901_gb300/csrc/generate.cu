@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "internal.h"
 
@@ -11,6 +12,34 @@ namespace si {
 
 namespace {
 bool valid_group(int g) { return g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32; }
+
+__global__ void iota_kernel(int32_t *q, int64_t m) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        q[i] = (int32_t)i;
+}
+
+// One non-blocking stream per device for si_generate_host's image downloads.
+cudaStream_t download_stream(int dev, cudaError_t *err) {
+    static std::mutex mu;
+    static cudaStream_t streams[128] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    *err = cudaSuccess;
+    if (dev < 0 || dev >= 128) {
+        *err = cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    if (!streams[dev]) *err = cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
+    return streams[dev];
+}
+
+// si_generate_host splits calls of at least kPipeMinImages images into
+// kPipeChunks query ranges: the download of one range's images overlaps the
+// generation of the next.
+#ifndef SI_PIPE_CHUNKS
+#define SI_PIPE_CHUNKS 2
+#endif
+constexpr int64_t kPipeMinImages = 32768;
+constexpr int kPipeChunks = SI_PIPE_CHUNKS;
 }  // namespace
 
 si_status check_item(const si_batch_item &it, const si_schedule &sc, int dev) {
@@ -120,8 +149,36 @@ si_status si_generate_host(const float *points, const float *normals, int64_t n,
     si_status st = si_mesh_create(points, normals, n, stream, &mesh);
     if (st != SI_OK) return st;
     int32_t *d_q = nullptr, *d_out = nullptr;
-    const size_t out_bytes = sizeof(int32_t) * (size_t)m * W * W;
+    const size_t img_words = (size_t)W * W;
+    const size_t out_bytes = sizeof(int32_t) * (size_t)m * img_words;
+    // A large call whose output is page-locked host memory mapped into the
+    // device's address space is written there by the kernel itself, over the
+    // host link, while it runs (no download afterwards); whole groups only, so
+    // no atomics go to host memory.
+    int32_t *direct = nullptr;
+    if (m >= kPipeMinImages) {
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, out) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer)
+            direct = static_cast<int32_t *>(pa.devicePointer);
+        cudaGetLastError();  // clear a failed attribute query
+    }
+    const int chunks = direct ? 1 : (m >= kPipeMinImages ? kPipeChunks : 1);
+    cudaEvent_t ev[kPipeChunks + 1] = {};
     do {
+        if (direct) {
+            if (query_idx) {
+                if ((st = dev_alloc((void **)&d_q, sizeof(int32_t) * m, s)) != SI_OK) break;
+                cudaError_t e = cudaMemcpyAsync(d_q, query_idx, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s);
+                if (e != cudaSuccess) {
+                    st = cuda_fail(e, "query upload");
+                    break;
+                }
+            }
+            si_schedule whole = schedule;
+            whole.slices = 1;
+            st = si_generate(mesh, d_q, m, W, bin_size, cos_support_angle, whole, direct, stream);
+            break;
+        }
         if (query_idx && m > 0) {
             if ((st = dev_alloc((void **)&d_q, sizeof(int32_t) * m, s)) != SI_OK) break;
             cudaError_t e = cudaMemcpyAsync(d_q, query_idx, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s);
@@ -129,22 +186,63 @@ si_status si_generate_host(const float *points, const float *normals, int64_t n,
                 st = cuda_fail(e, "query upload");
                 break;
             }
-        }
-        if ((st = dev_alloc((void **)&d_out, out_bytes, s)) != SI_OK) break;
-        st = si_generate(mesh, d_q, m, W, bin_size, cos_support_angle, schedule, d_out, stream);
-        if (st != SI_OK) break;
-        if (m > 0) {
-            cudaError_t e = cudaMemcpyAsync(out, d_out, out_bytes, cudaMemcpyDeviceToHost, s);
+        } else if (chunks > 1) {
+            // query ranges of the all-points call as explicit index lists
+            if ((st = dev_alloc((void **)&d_q, sizeof(int32_t) * m, s)) != SI_OK) break;
+            iota_kernel<<<256, 256, 0, s>>>(d_q, m);
+            note_launches(1);
+            cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) {
-                st = cuda_fail(e, "image download");
+                st = cuda_fail(e, "iota_kernel");
                 break;
             }
         }
+        if ((st = dev_alloc((void **)&d_out, out_bytes, s)) != SI_OK) break;
+        if (chunks == 1) {
+            st = si_generate(mesh, d_q, m, W, bin_size, cos_support_angle, schedule, d_out, stream);
+            if (st != SI_OK) break;
+            if (m > 0) {
+                cudaError_t e = cudaMemcpyAsync(out, d_out, out_bytes, cudaMemcpyDeviceToHost, s);
+                if (e != cudaSuccess) {
+                    st = cuda_fail(e, "image download");
+                    break;
+                }
+            }
+            break;
+        }
+        // generate range k on `s` while the download stream copies range k-1 out
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        cudaStream_t cs = e == cudaSuccess ? download_stream(dev, &e) : nullptr;
+        for (int k = 0; k <= chunks && e == cudaSuccess; ++k)
+            e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "download stream / events");
+            break;
+        }
+        for (int k = 0; k < chunks && st == SI_OK; ++k) {
+            const int64_t a = m * k / chunks, b = m * (k + 1) / chunks;
+            st = si_generate(mesh, d_q + a, b - a, W, bin_size, cos_support_angle, schedule, d_out + a * img_words,
+                             stream);
+            if (st != SI_OK) break;
+            e = cudaEventRecord(ev[k], s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[k], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(out + a * img_words, d_out + a * img_words,
+                                    sizeof(int32_t) * (size_t)(b - a) * img_words, cudaMemcpyDeviceToHost, cs);
+            if (e != cudaSuccess) st = cuda_fail(e, "image download");
+        }
+        // the output buffer is released on `s`, after the last download
+        e = cudaEventRecord(ev[chunks], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[chunks], 0);
+        if (e != cudaSuccess && st == SI_OK) st = cuda_fail(e, "download completion");
     } while (0);
     if (d_q) dev_free(d_q, s);
     if (d_out) dev_free(d_out, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess && st == SI_OK) st = cuda_fail(e, "cudaStreamSynchronize");
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
     si_stats stats;
     si_status st2 = si_get_stats(mesh, &stats);
     si_mesh_destroy(mesh);

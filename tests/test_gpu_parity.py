@@ -260,6 +260,30 @@ def test_host_buffer_path_equals_device_path():
     np.testing.assert_array_equal(out.numpy(), ref)
 
 
+@pytest.mark.parametrize("explicit,pinned", [(False, True), (True, True), (False, False), (True, False)])
+def test_host_buffer_path_large_calls(explicit, pinned):
+    """Calls of 32,768 images or more: into page-locked output the kernel
+    writes directly; into pageable output the call generates in query ranges
+    whose downloads overlap the next range's generation.  Images equal the
+    device path's either way."""
+    import torch
+
+    import paper_1811_00901_gb300 as spin
+    n = 40_000
+    pts, nrm = wl.heightfield(n, 15)
+    W, B, c = 16, 0.02, 0.5
+    q = np.random.default_rng(1).permutation(n)[:36_001].astype(np.int32) if explicit else None
+    m = n if q is None else len(q)
+    ref, _ = gpu_run(pts, nrm, W, B, c, query_idx=q)
+    out = torch.full((m, W, W), -3, dtype=torch.int32)
+    if pinned:
+        out = out.pin_memory()
+    tq = None if q is None else torch.from_numpy(q)
+    spin.si_generate_host(torch.from_numpy(pts), torch.from_numpy(nrm), n, tq, m, W, B, c,
+                          spin.make_schedule("FAC"), out)
+    np.testing.assert_array_equal(out.numpy(), ref)
+
+
 def test_batched_equals_single_calls():
     import torch
 
