@@ -336,7 +336,8 @@ def run_ours(args):
             et.append(time.perf_counter() - t0)
         e2e = {"value": m / statistics.median(et), "unit": UNIT, "h2d_bytes_per_step": int(2 * n * 3 * 4),
                "d2h_bytes_per_step": int(m * W * W * 4), "ms_per_step": 1e3 * statistics.median(et),
-               "api": "si_generate_host (host buffers, copies and mesh/grid build inside)"}
+               "api": "si_generate_host (host buffers; mesh/grid build inside; the kernel writes the images "
+                      "straight into the page-locked host output)"}
 
     # ---- roofline of the spin kernel (the dominant kernel)
     peaks, peak_src = _measured_peaks()
