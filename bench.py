@@ -389,15 +389,16 @@ def run_ours(args):
         # probabilistic factoring with sigma / mu of the group cost measured by
         # the probe run (a group's cost follows its candidate stream length)
         cov = _group_cost_cov(examined_per_image)
-        extra["fac-prob-heightfield-100k-W32"] = dict(
+        extra["factoring-heightfield-100k-W32"] = dict(
             bench_single(spin, torch, dev, c, ex_steps, args.warmup, flush, stream, scheds={
                 "FAC": spin.make_schedule("FAC", **shape),
-                "FAC_PROB": spin.make_schedule("FAC_PROB", fac_cov=cov, **shape)}), fac_cov=cov)
+                "FAC_PROB": spin.make_schedule("FAC_PROB", fac_cov=cov, **shape),
+                "AWF": spin.make_schedule("AWF", **shape)}), fac_cov=cov)
         # heterogeneity emulation (Sec. 5.2's Type2 + Type1 runs): the first half
         # of the workers 3x slower, and they request first
         P = sms_count(torch, dev) * 3
         het = {k: spin.make_schedule(k, num_workers=P, slow_workers=P // 2, slowdown=3.0, fac_cov=cov, **shape)
-               for k in ("STATIC", "SS", "GSS", "FAC", "FAC_PROB")}
+               for k in ("STATIC", "SS", "GSS", "FAC", "FAC_PROB", "AWF")}
         h = bench_single(spin, torch, dev, c, ex_steps, args.warmup, flush, stream, scheds=het)
         h["emulation"] = {"workers": P, "slow_workers": P // 2, "slowdown": 3.0, "slow_request_first": True}
         h["over_static"] = {k: v["images_per_s"] / h["by_schedule"]["STATIC"]["images_per_s"]

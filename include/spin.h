@@ -79,7 +79,16 @@ typedef enum si_sched_kind {
                              b_j = P / (2 sqrt(R_j)) * cov, x_0 = 1 + b_0^2 + b_0 sqrt(b_0^2 + 2),
                              x_j = 2 + b_j^2 + b_j sqrt(b_j^2 + 4) (j >= 1), cov = sigma / mu of the
                              iteration time (si_schedule.fac_cov), evaluated in IEEE double;
-                             >= min_chunk */
+                             >= min_chunk */,
+    SI_SCHED_AWF = 5      /* adaptive weighted factoring: batches of P chunks as FAC (the FAC2 chunk
+                             of each batch, computed for the call's whole loop), each chunk scaled by
+                             the requesting worker's weight w = rate / (mean rate of the workers
+                             measured so far), rate = its groups done / its time so far (measured on
+                             the device, updated after every chunk; w = 1 before a worker's first
+                             chunk ends; w clamped to [0.05, 20]); chunk = max(min_chunk,
+                             round(w x batch chunk)).  Chunk sizes depend on measured times and are
+                             decided on the device; every group is still generated exactly once.
+                             In a batched call every item must use it. */
 } si_sched_kind;
 
 /* How a contributing pair is counted into its image. */
@@ -244,7 +253,8 @@ si_status si_chunk_table(int32_t kind, int64_t units, int32_t workers, int32_t m
 
 /* si_chunk_table for a whole schedule (kind, min_chunk and, for
  * SI_SCHED_FAC_PROB, fac_cov); si_chunk_table(kind, ...) is this with
- * fac_cov = 0. */
+ * fac_cov = 0.  SI_SCHED_AWF has no table (its chunks are decided on the
+ * device): SI_ERR_INVALID. */
 si_status si_schedule_chunks(const si_schedule *schedule, int64_t units, int32_t workers, int64_t *starts,
                              int64_t capacity, int64_t *nsteps);
 

@@ -121,6 +121,10 @@ struct Plan {
     int slow_workers = 0;
     float slowdown = 1.0f;
     std::vector<int> binning;  // per item: si_binning
+    // adaptive weighted factoring: unit bases of the items and FAC2 batch chunks
+    bool awf = false;
+    int awf_min_chunk = 1;
+    std::vector<int> awf_ubase, awf_batch;
     bool all_static = true;
     int nsteps = 0;
     std::vector<Piece> pieces;
@@ -136,7 +140,8 @@ struct Plan {
     std::vector<int64_t> split_base, counts_off;
     int64_t split_images = 0;
     size_t o_ctr = 0, o_items = 0, o_pieces = 0, o_steps = 0, o_sitems = 0, o_sqbase = 0, o_split = 0,
-           o_split_items = 0, o_hist = 0, o_perm = 0, o_counts = 0, total_bytes = 0;
+           o_split_items = 0, o_awf_ubase = 0, o_awf_batch = 0, o_hist = 0, o_perm = 0, o_counts = 0,
+           total_bytes = 0;
     bool empty = false;
 };
 
@@ -228,10 +233,36 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
     p->split_base.push_back(p->split_images);
 
     // ---- the scheduled loop: steps made of pieces
-    for (int k = 0; k < nitems; ++k)
+    int n_awf = 0, n_used = 0;
+    for (int k = 0; k < nitems; ++k) {
         if (items[k].m > 0 && scheds[k].kind != SI_SCHED_STATIC) p->all_static = false;
+        if (items[k].m > 0) {
+            ++n_used;
+            if (scheds[k].kind == SI_SCHED_AWF) ++n_awf;
+        }
+    }
+    if (n_awf > 0 && n_awf != n_used) {
+        set_error("adaptive weighted factoring must be the rule of every item of a call");
+        return SI_ERR_INVALID;
+    }
     p->step_piece.assign(1, 0);
-    if (p->all_static) {
+    if (n_awf > 0) {
+        // one loop over the concatenated units, chunk sizes decided on the device
+        p->awf = true;
+        p->awf_ubase.assign(nitems + 1, 0);
+        for (int k = 0; k < nitems; ++k) p->awf_ubase[k + 1] = p->awf_ubase[k] + p->units[k];
+        int mc = 1;
+        for (int k = 0; k < nitems; ++k)
+            if (items[k].m > 0) {
+                mc = std::max(1, scheds[k].min_chunk);
+                break;
+            }
+        p->awf_min_chunk = mc;
+        std::vector<int64_t> st;
+        chunk_table(SI_SCHED_FAC, total_units, workers, mc, 0.0, &st);
+        for (size_t s = 0; s + 1 < st.size(); s += (size_t)workers) p->awf_batch.push_back((int)(st[s + 1] - st[s]));
+        p->nsteps = 0;
+    } else if (p->all_static) {
         // PSIA: block b gets the contiguous block [floor(bU/P), floor((b+1)U/P)) of
         // the concatenated group space; a block may span item boundaries.
         std::vector<int64_t> ubase(nitems + 1, 0);
@@ -267,7 +298,7 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
             }
         }
     }
-    p->nsteps = (int)p->step_piece.size() - 1;
+    if (!p->awf) p->nsteps = (int)p->step_piece.size() - 1;
 
     // ---- query sorting (items that are not "all points of the mesh")
     p->sort_of.assign(nitems, -1);
@@ -309,7 +340,9 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
     p->o_sqbase = align_up(p->o_sitems + sizeof(SortItem) * p->sitems.size(), 256);
     p->o_split = align_up(p->o_sqbase + sizeof(int64_t) * p->sqbase.size(), 256);
     p->o_split_items = align_up(p->o_split + sizeof(int64_t) * p->split_base.size(), 256);
-    p->o_hist = align_up(p->o_split_items + sizeof(int) * p->split_items.size(), 256);
+    p->o_awf_ubase = align_up(p->o_split_items + sizeof(int) * p->split_items.size(), 256);
+    p->o_awf_batch = align_up(p->o_awf_ubase + sizeof(int) * p->awf_ubase.size(), 256);
+    p->o_hist = align_up(p->o_awf_batch + sizeof(int) * p->awf_batch.size(), 256);
     p->o_perm = align_up(p->o_hist + sizeof(int) * (p->htot + 1), 256);
     p->o_counts = align_up(p->o_perm + sizeof(int) * p->qtot, 256);
     p->total_bytes = align_up(p->o_counts + sizeof(int) * p->split_images, 256);
@@ -392,6 +425,10 @@ void fill_blob(const Plan &p, const std::vector<si_batch_item> &items, const std
         std::memcpy(h + (p.o_split - p.o_items), p.split_base.data(), sizeof(int64_t) * p.split_base.size());
         std::memcpy(h + (p.o_split_items - p.o_items), p.split_items.data(), sizeof(int) * p.split_items.size());
     }
+    if (p.awf) {
+        std::memcpy(h + (p.o_awf_ubase - p.o_items), p.awf_ubase.data(), sizeof(int) * p.awf_ubase.size());
+        std::memcpy(h + (p.o_awf_batch - p.o_items), p.awf_batch.data(), sizeof(int) * p.awf_batch.size());
+    }
 }
 
 // Device commands of a planned batch on `stream` (also what a graph captures).
@@ -444,6 +481,14 @@ si_status record_batch(const Plan &p, const std::vector<si_batch_item> &items, c
     a.img_words = (int)p.max_img_words;
     a.probe = probe ? 1 : 0;
     a.modes = p.modes;
+    if (p.awf) {
+        a.awf = 1;
+        a.total_units = p.awf_ubase.back();
+        a.unit_base = reinterpret_cast<const int *>(scratch + p.o_awf_ubase);
+        a.awf_batch = reinterpret_cast<const int *>(scratch + p.o_awf_batch);
+        a.awf_nbatch = (int)p.awf_batch.size();
+        a.min_chunk = p.awf_min_chunk;
+    }
     // heterogeneity emulation: at most every launched block is slow
     const int blocks = p.all_static ? p.nsteps : p.workers;
     a.slow_workers = std::min(p.slow_workers, blocks);

@@ -141,6 +141,11 @@ struct Piece {
 struct LaunchCounters {
     unsigned long long step;         // next dynamic step to hand out
     unsigned long long done_blocks;  // blocks finished
+    unsigned long long awf_next;     // AWF: next unit of the call's concatenated unit space
+    unsigned long long awf_claims;   // AWF: chunks handed out
+    double awf_rate_sum;             // AWF: sum of the measured worker rates (units per ns)
+    unsigned awf_rated;              // AWF: workers with a measured rate
+    unsigned pad;
 };
 
 struct LaunchArgs {
@@ -156,6 +161,13 @@ struct LaunchArgs {
     int slow_workers = 0;   // heterogeneity emulation: blocks 0..slow_workers-1 are slow and request first
     float slowdown = 1.0f;  // a slow block idles (slowdown - 1) x each step's time
     int modes = 0;          // tile-ring disciplines present (kModeBarrier | kModeProducer); 0 = both
+    // adaptive weighted factoring (chunk sizes decided on the device)
+    int awf = 0;
+    int total_units = 0;             // units of all items
+    const int *unit_base = nullptr;  // [nitems + 1]: first unit of each item in the concatenation
+    const int *awf_batch = nullptr;  // FAC2 chunk of batch j, j < awf_nbatch
+    int awf_nbatch = 0;
+    int min_chunk = 1;
 };
 
 // Tile-ring discipline of a group shape: groups of <= 4 images run a producer

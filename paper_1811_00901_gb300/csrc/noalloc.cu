@@ -145,7 +145,7 @@ extern "C" si_status si_generate_noalloc(si_mesh_t mesh, const int32_t *query_id
     const si_batch_item it{mesh, query_idx, m, W, bin_size, cos_support_angle, out};
     si_status s = check_item(it, schedule, dev);
     if (s != SI_OK) return s;
-    if (schedule.kind == SI_SCHED_FAC_PROB || schedule.binning != SI_BIN_BILINEAR || schedule.slow_workers != 0) {
+    if (schedule.kind >= SI_SCHED_FAC_PROB || schedule.binning != SI_BIN_BILINEAR || schedule.slow_workers != 0) {
         set_error("si_generate_noalloc: takes STATIC, SS, GSS or FAC, bilinear binning and no slow workers");
         return SI_ERR_INVALID;
     }

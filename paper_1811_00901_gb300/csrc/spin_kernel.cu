@@ -71,6 +71,12 @@ struct __align__(16) Header {
     int slot_cnt[32];         // sliced groups: contributing pairs per image of this slice
     int cur_r, cur_o;          // barrier mode: producer row cursor
     unsigned long long t_step;  // heterogeneity emulation: start of a slow block's step
+    // adaptive weighted factoring: this worker's claim and its measured rate
+    int awf_lo, awf_hi;
+    unsigned long long awf_t0;  // when the current chunk was claimed
+    double awf_units, awf_ns;   // units done and time spent so far
+    double awf_rate;            // awf_units / awf_ns (0: not measured yet)
+    int awf_last;               // units of the current chunk
 };
 
 constexpr int kHeaderBytes = (sizeof(Header) + 127) / 128 * 128;
@@ -705,6 +711,43 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
     return true;
 }
 
+// Adaptive weighted factoring, the request half of getChunk run on the device
+// by thread 0 of a worker: fold the chunk just finished into the worker's
+// rate, take the next claim's FAC2 batch chunk, scale it by the worker's
+// weight (its rate over the mean of the measured rates) and take that many
+// units from the shared cursor.  Sets H.claim (the claim index), H.awf_lo and
+// H.awf_hi.
+__device__ void awf_claim(const LaunchArgs &a, Header &H, const int claim_iter, const bool first_slow) {
+    const uint64_t now = global_ns();
+    if (claim_iter > 0 && H.awf_last > 0) {
+        H.awf_units += (double)H.awf_last;
+        H.awf_ns += (double)(now - H.awf_t0);
+        const double rate = H.awf_units / fmax(H.awf_ns, 1.0);
+        atomicAdd(&a.ctr->awf_rate_sum, rate - H.awf_rate);
+        if (H.awf_rate == 0.0) atomicAdd(&a.ctr->awf_rated, 1u);
+        H.awf_rate = rate;
+    }
+    // slow workers (heterogeneity emulation) request first: claim k is slow worker k's
+    const unsigned long long s =
+        first_slow ? (unsigned long long)blockIdx.x
+                   : (unsigned long long)a.slow_workers + atomicAdd(&a.ctr->awf_claims, 1ull);
+    const unsigned long long j = s / gridDim.x;
+    const int batch = j < (unsigned long long)a.awf_nbatch ? a.awf_batch[j] : a.min_chunk;
+    double w = 1.0;
+    const unsigned rated = *(volatile unsigned *)&a.ctr->awf_rated;
+    const double sum = *(volatile double *)&a.ctr->awf_rate_sum;
+    if (H.awf_rate > 0.0 && rated > 0 && sum > 0.0) w = fmin(fmax(H.awf_rate * (double)rated / sum, 0.05), 20.0);
+    const int chunk = max(a.min_chunk, (int)(w * (double)batch + 0.5));
+    const unsigned long long lo = atomicAdd(&a.ctr->awf_next, (unsigned long long)chunk);
+    const int total = a.total_units;
+    H.awf_lo = lo >= (unsigned long long)total ? total : (int)lo;
+    H.awf_hi = lo >= (unsigned long long)total ? total : (int)min(lo + (unsigned long long)chunk,
+                                                                   (unsigned long long)total);
+    H.awf_last = H.awf_hi - H.awf_lo;
+    H.awf_t0 = now;
+    H.claim = (int)s;
+}
+
 // MODES: the paths compiled in (kModeBarrier | kModeProducer | kModeNearest);
 // a launch whose groups all use one discipline runs the instance without the
 // other, whose registers are then allocated for its own loop alone.  Groups
@@ -754,70 +797,117 @@ __global__ void __launch_bounds__(kThreads, min_blocks_for<MODES>()) spin_kernel
     // heterogeneity emulation: slow blocks (index < a.slow_workers) take the
     // first steps, one each, and the shared counter hands out the steps after
     // them; H.t_step holds the start of a slow block's current step
+    if (tid == 0) {
+        H.awf_units = 0.0;
+        H.awf_ns = 0.0;
+        H.awf_rate = 0.0;
+    }
+
+    // generates units [u0, u1) of item `item`; `step` is the claim they came from
+    auto run = [&](const int item, const int u0, const int u1, const int step) {
+        const ItemDesc &it = a.items[item];
+        const int key = it.W * 8 + it.log2S;
+        for (int u = u0; u < u1 && alive; ++u) {
+            // specialised shapes for the common widths, a runtime one otherwise;
+            // the nearest-bin count runs on the runtime shape
+            if ((MODES & kModeNearest) != 0 && it.binning == SI_BIN_NEAREST) {
+                if constexpr ((MODES & kModeNearest) != 0) {
+                    alive = it.log2S <= 2 ? process_group<0, 0, PROBE, true, true>(it, u, step, sv, phase_bits)
+                                          : process_group<0, 0, PROBE, false, true>(it, u, step, sv, phase_bits);
+                }
+            } else if (it.log2S <= 2) {
+                if constexpr ((MODES & kModeProducer) != 0) {
+                    switch (key) {
+                        case 64 * 8 + 1:
+                            alive = process_group<64, 1, PROBE, true>(it, u, step, sv, phase_bits);
+                            break;
+                        case 64 * 8 + 2:
+                            alive = process_group<64, 2, PROBE, true>(it, u, step, sv, phase_bits);
+                            break;
+                        default:
+                            alive = process_group<0, 0, PROBE, true>(it, u, step, sv, phase_bits);
+                            break;
+                    }
+                }
+            } else {
+                if constexpr ((MODES & kModeBarrier) != 0) {
+                    switch (key) {
+                        case 16 * 8 + 5:
+                            alive = process_group<16, 5, PROBE, false>(it, u, step, sv, phase_bits);
+                            break;
+                        case 32 * 8 + 4:
+                            alive = process_group<32, 4, PROBE, false>(it, u, step, sv, phase_bits);
+                            break;
+                        case 32 * 8 + 3:
+                            alive = process_group<32, 3, PROBE, false>(it, u, step, sv, phase_bits);
+                            break;
+                        default:
+                            alive = process_group<0, 0, PROBE, false>(it, u, step, sv, phase_bits);
+                            break;
+                    }
+                }
+            }
+        }
+    };
 
     while (alive) {
         __syncthreads();
         if (tid == 0) {
-            int s;
-            if (a.is_static)
-                s = claim_iter == 0 ? (int)blockIdx.x : a.nsteps;
-            else if ((int)blockIdx.x < a.slow_workers && claim_iter == 0)
-                s = (int)blockIdx.x;
-            else
-                s = a.slow_workers + (int)atomicAdd(&a.ctr->step, 1ull);
-            H.claim = s;
+            const bool first_slow = (int)blockIdx.x < a.slow_workers && claim_iter == 0;
+            if (a.awf) {
+                awf_claim(a, H, claim_iter, first_slow);
+            } else {
+                int s;
+                if (a.is_static)
+                    s = claim_iter == 0 ? (int)blockIdx.x : a.nsteps;
+                else if (first_slow)
+                    s = (int)blockIdx.x;
+                else
+                    s = a.slow_workers + (int)atomicAdd(&a.ctr->step, 1ull);
+                H.claim = s;
+            }
             if ((int)blockIdx.x < a.slow_workers) H.t_step = global_ns();
         }
         __syncthreads();
         const int step = H.claim;
         ++claim_iter;
-        if (step >= a.nsteps) break;
-
-        for (int pi = a.step_piece[step]; pi < a.step_piece[step + 1] && alive; ++pi) {
-            const Piece pc = a.pieces[pi];
-            const ItemDesc &it = a.items[pc.item];
-            const int key = it.W * 8 + it.log2S;
-            for (int u = pc.u0; u < pc.u1 && alive; ++u) {
-                // specialised shapes for the common widths, a runtime one otherwise;
-                // the nearest-bin count runs on the runtime shape
-                if ((MODES & kModeNearest) != 0 && it.binning == SI_BIN_NEAREST) {
-                    if constexpr ((MODES & kModeNearest) != 0) {
-                        alive = it.log2S <= 2 ? process_group<0, 0, PROBE, true, true>(it, u, step, sv, phase_bits)
-                                              : process_group<0, 0, PROBE, false, true>(it, u, step, sv, phase_bits);
-                    }
-                } else if (it.log2S <= 2) {
-                    if constexpr ((MODES & kModeProducer) != 0) {
-                        switch (key) {
-                            case 64 * 8 + 1:
-                                alive = process_group<64, 1, PROBE, true>(it, u, step, sv, phase_bits);
-                                break;
-                            case 64 * 8 + 2:
-                                alive = process_group<64, 2, PROBE, true>(it, u, step, sv, phase_bits);
-                                break;
-                            default:
-                                alive = process_group<0, 0, PROBE, true>(it, u, step, sv, phase_bits);
-                                break;
-                        }
-                    }
-                } else {
-                    if constexpr ((MODES & kModeBarrier) != 0) {
-                        switch (key) {
-                            case 16 * 8 + 5:
-                                alive = process_group<16, 5, PROBE, false>(it, u, step, sv, phase_bits);
-                                break;
-                            case 32 * 8 + 4:
-                                alive = process_group<32, 4, PROBE, false>(it, u, step, sv, phase_bits);
-                                break;
-                            case 32 * 8 + 3:
-                                alive = process_group<32, 3, PROBE, false>(it, u, step, sv, phase_bits);
-                                break;
-                            default:
-                                alive = process_group<0, 0, PROBE, false>(it, u, step, sv, phase_bits);
-                                break;
-                        }
-                    }
+        // the claim as ranges of one item each: the step's pieces, or (AWF) the
+        // units [H.awf_lo, H.awf_hi) of the concatenated unit space
+        int pi = 0, pend = 0, g = 0, ghi = 0;
+        if (a.awf) {
+            g = H.awf_lo;
+            ghi = H.awf_hi;
+            if (g >= ghi) break;
+        } else {
+            if (step >= a.nsteps) break;
+            pi = a.step_piece[step];
+            pend = a.step_piece[step + 1];
+        }
+        while (alive) {
+            int item, u0, u1;
+            if (a.awf) {
+                if (g >= ghi) break;
+                int lo_k = 0, hi_k = a.nitems - 1;  // the last item whose first unit is <= g
+                while (lo_k < hi_k) {
+                    const int mid = (lo_k + hi_k + 1) >> 1;
+                    if (a.unit_base[mid] <= g)
+                        lo_k = mid;
+                    else
+                        hi_k = mid - 1;
                 }
+                const int base = a.unit_base[lo_k], end = min(ghi, a.unit_base[lo_k + 1]);
+                item = lo_k;
+                u0 = g - base;
+                u1 = end - base;
+                g = end;
+            } else {
+                if (pi >= pend) break;
+                const Piece pc = a.pieces[pi++];
+                item = pc.item;
+                u0 = pc.u0;
+                u1 = pc.u1;
             }
+            run(item, u0, u1, step);
         }
         if ((int)blockIdx.x < a.slow_workers && alive && tid == 0) {
             // a slow worker idles (slowdown - 1) x the time of its step, at most
@@ -836,6 +926,10 @@ __global__ void __launch_bounds__(kThreads, min_blocks_for<MODES>()) spin_kernel
         const unsigned long long prev = atomicAdd(&a.ctr->done_blocks, 1ull);
         if (prev == gridDim.x - 1) {
             atomicExch(&a.ctr->step, 0ull);
+            atomicExch(&a.ctr->awf_next, 0ull);
+            atomicExch(&a.ctr->awf_claims, 0ull);
+            atomicExch(reinterpret_cast<unsigned long long *>(&a.ctr->awf_rate_sum), 0ull);  // +0.0
+            atomicExch(&a.ctr->awf_rated, 0u);
             atomicExch(&a.ctr->done_blocks, 0ull);
         }
     }

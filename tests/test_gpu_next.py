@@ -1,7 +1,8 @@
-"""The scheduling extensions: probabilistic factoring (FAC_PROB) and the
-heterogeneity emulation of the paper's Type1 + Type2 runs (Sec. 5.2).
-Neither may change an image; FAC_PROB's steps follow its chunk table; slow
-workers take the first steps."""
+"""The scheduling extensions: probabilistic factoring (FAC_PROB), adaptive
+weighted factoring (AWF, chunk sizes decided on the device) and the
+heterogeneity emulation of the paper's Type1 + Type2 runs (Sec. 5.2).  None
+may change an image; FAC_PROB's steps follow its chunk table; AWF hands out
+every group exactly once; slow workers take the first steps."""
 import numpy as np
 import pytest
 
@@ -45,7 +46,7 @@ def test_fac_prob_images_and_steps():
             assert per_step[s] == max(0, hi - lo), (cov, s)
 
 
-@pytest.mark.parametrize("kind", ["STATIC", "SS", "GSS", "FAC", "FAC_PROB"])
+@pytest.mark.parametrize("kind", ["STATIC", "SS", "GSS", "FAC", "FAC_PROB", "AWF"])
 def test_slow_workers_change_no_image_and_take_the_first_steps(kind):
     import paper_1811_00901_gb300 as spin
     pts, nrm = wl.heightfield(6000, 12)
@@ -94,5 +95,80 @@ def test_slow_workers_slow_static_down_more_than_self_scheduling():
         het_ss = kernel_ms(spin.make_schedule("SS", num_workers=P, slow_workers=P // 2, slowdown=6.0))
         assert het_static > 3.0 * hom, (hom, het_static)
         assert het_ss < 0.6 * het_static, (het_ss, het_static)
+    finally:
+        spin.si_mesh_destroy(mesh)
+
+
+@pytest.mark.parametrize("group,workers,slices,mc", [(8, 0, 1, 1), (1, 37, 0, 1), (32, 300, 1, 3), (4, 9, 4, 2)])
+def test_awf_generates_every_group_once(group, workers, slices, mc):
+    """AWF: images equal STATIC's; each image comes from exactly one claim and
+    the claims' images form contiguous group ranges of the loop."""
+    import paper_1811_00901_gb300 as spin
+    pts, nrm = wl.heightfield(5000, 31)
+    W, B, c = 16, 0.02, 0.5
+    ref, _ = gpu_run(pts, nrm, W, B, c, schedule=spin.make_schedule("STATIC"))
+    img, pr = gpu_run(pts, nrm, W, B, c, probe=True,
+                      schedule=spin.make_schedule("AWF", group=group, num_workers=workers, slices=slices,
+                                                  min_chunk=mc))
+    np.testing.assert_array_equal(img, ref)
+    assert (pr["step"] >= 0).all() and (pr["worker"] >= 0).all()
+    # a claim is one worker's
+    for s in np.unique(pr["step"]):
+        assert len(np.unique(pr["worker"][pr["step"] == s])) == 1
+
+
+def test_awf_batched_items_share_one_loop():
+    import torch
+
+    import paper_1811_00901_gb300 as spin
+    dev = torch.device("cuda:0")
+    meshes, items, refs = [], [], []
+    try:
+        for k, (n, W, B, cs) in enumerate([(3000, 16, 0.05, 0.5), (1500, 32, 0.025, 0.0), (0, 16, 0.05, 0.5),
+                                           (900, 7, 0.1, -1.0)]):
+            pts, nrm = wl.sphere(max(n, 10), 50 + k)
+            mh = spin.si_mesh_create(torch.from_numpy(pts).to(dev), torch.from_numpy(nrm).to(dev))
+            meshes.append(mh)
+            out = torch.empty((n, W, W), dtype=torch.int32, device=dev)
+            items.append(dict(mesh=mh, query_idx=None, m=n, W=W, bin_size=B, cos_s=cs, out=out))
+            refs.append(gpu_run(pts, nrm, W, B, cs, m=n, schedule=spin.make_schedule("STATIC"))[0])
+        spin.si_generate_batched(items, spin.make_schedule("AWF"))
+        torch.cuda.synchronize()
+        for it, ref in zip(items, refs):
+            np.testing.assert_array_equal(it["out"].cpu().numpy(), ref)
+    finally:
+        for mh in meshes:
+            spin.si_mesh_destroy(mh)
+
+
+def test_awf_beats_fac_with_slow_workers():
+    """With half the workers 4x slower, AWF's weights shrink the slow workers'
+    chunks: it finishes no later than FAC (within 10 %)."""
+    import torch
+
+    import paper_1811_00901_gb300 as spin
+    pts, nrm = wl.heightfield(30_000, 14)
+    W, B, c = 32, 0.01, wl.cos_deg(60.0)
+    dev = torch.device("cuda:0")
+    mesh = spin.si_mesh_create(torch.from_numpy(pts).to(dev), torch.from_numpy(nrm).to(dev))
+    out = torch.empty((30_000, W, W), dtype=torch.int32, device=dev)
+
+    def kernel_ms(sched):
+        spin.si_generate(mesh, None, 30_000, W, B, c, sched, out)
+        torch.cuda.synchronize()
+        spin.si_reset_stats(mesh)
+        spin.si_set_timing(True)
+        for _ in range(3):
+            spin.si_generate(mesh, None, 30_000, W, B, c, sched, out)
+        torch.cuda.synchronize()
+        st, _ = spin.si_get_stats(mesh)
+        spin.si_set_timing(False)
+        return st["kernel_ms"] / st["kernel_launches"]
+
+    try:
+        P = 152 * 3
+        fac = kernel_ms(spin.make_schedule("FAC", num_workers=P, slow_workers=P // 2, slowdown=4.0))
+        awf = kernel_ms(spin.make_schedule("AWF", num_workers=P, slow_workers=P // 2, slowdown=4.0))
+        assert awf <= 1.1 * fac, (awf, fac)
     finally:
         spin.si_mesh_destroy(mesh)
