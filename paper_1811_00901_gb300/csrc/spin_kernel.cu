@@ -808,12 +808,16 @@ __global__ void __launch_bounds__(kThreads, min_blocks_for<MODES>()) spin_kernel
         const ItemDesc &it = a.items[item];
         const int key = it.W * 8 + it.log2S;
         for (int u = u0; u < u1 && alive; ++u) {
-            // specialised shapes for the common widths, a runtime one otherwise;
-            // the nearest-bin count runs on the runtime shape
+            // specialised shapes for the common widths, a runtime one otherwise
+            // (the nearest-bin count: W = 32 in groups of 8, else the runtime shape)
             if ((MODES & kModeNearest) != 0 && it.binning == SI_BIN_NEAREST) {
                 if constexpr ((MODES & kModeNearest) != 0) {
-                    alive = it.log2S <= 2 ? process_group<0, 0, PROBE, true, true>(it, u, step, sv, phase_bits)
-                                          : process_group<0, 0, PROBE, false, true>(it, u, step, sv, phase_bits);
+                    if (key == 32 * 8 + 3)
+                        alive = process_group<32, 3, PROBE, false, true>(it, u, step, sv, phase_bits);
+                    else if (it.log2S <= 2)
+                        alive = process_group<0, 0, PROBE, true, true>(it, u, step, sv, phase_bits);
+                    else
+                        alive = process_group<0, 0, PROBE, false, true>(it, u, step, sv, phase_bits);
                 }
             } else if (it.log2S <= 2) {
                 if constexpr ((MODES & kModeProducer) != 0) {
