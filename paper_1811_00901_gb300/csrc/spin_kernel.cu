@@ -192,7 +192,10 @@ __device__ __forceinline__ void eval_pair(const PairDist &pd, const float4 NX, c
     const float beta = fmaf(N.z, dz, fmaf(N.y, dy, N.x * dx));
     const float a2 = fmaxf(fmaf(-beta, beta, d2), 0.0f);
     const float u = fmaf(-beta, k.invB, k.halfW);
-    const bool in = live & (ca >= k.cosS) & (u >= 0.0f) & (u < k.umax) & (a2 < k.amax2);
+    // 0 <= u < W-1 as one unsigned compare of the float bits: non-negative floats
+    // order like their bits, negatives (sign bit) and NaN compare above umax; u
+    // is never -0 (halfW - beta/B rounds an exact zero to +0)
+    const bool in = live & (ca >= k.cosS) & (__float_as_uint(u) < __float_as_uint(k.umax)) & (a2 < k.amax2);
     if (PROBE && in) atomicAdd(pc_s, 1);
     // alpha through the approximate reciprocal square root; the support
     // decision above does not depend on it, and 16-bit quantisation absorbs
@@ -213,9 +216,10 @@ __device__ __forceinline__ void eval_pair(const PairDist &pd, const float4 NX, c
     if (in) {
         const int rw = sh.row_words(), S = sh.S();
         int *p0 = img_adj + ((int)(Ub >> 16) * rw + (int)(Vb >> 16) * S);
-        atomicAdd(p0, (int)(65536u - A - Bq + w11));
+        const uint32_t w01 = Bq - w11;
+        atomicAdd(p0, (int)(65536u - A - w01));  // w00 = 2^16 - A - Bq + w11
         atomicAdd(p0 + rw, (int)(A - w11));
-        atomicAdd(p0 + S, (int)(Bq - w11));
+        atomicAdd(p0 + S, (int)w01);
         atomicAdd(p0 + rw + S, (int)w11);
         ++cnt;
     }
