@@ -32,6 +32,8 @@
 //   weight 65536 with four shared-memory int32 atomics.
 // Images hold (W+1) x (W+1) words per slot: the extra row and column absorb
 // the zero-weight corners of points whose coordinate rounds up onto W-1.
+#include <atomic>
+
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -955,8 +957,15 @@ size_t spin_smem_bytes(int W, int log2S) { return (size_t)shape_smem(W, log2S, t
 constexpr int kModeAll = kModeBarrier | kModeProducer | kModeNearest;
 
 cudaError_t setup_spin_kernel_attributes(size_t smem_bytes) {
-    static size_t done = 0;
-    if (smem_bytes <= done) return cudaSuccess;
+    // the attribute belongs to each device's context: remember it per device
+    constexpr int kMaxDevices = 128;
+    static std::atomic<size_t> done_per_device[kMaxDevices];
+    int dev = 0;
+    cudaError_t de = cudaGetDevice(&dev);
+    if (de != cudaSuccess) return de;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::atomic<size_t> &done_ref = done_per_device[dev];
+    if (smem_bytes <= done_ref.load()) return cudaSuccess;
     const int bytes = (int)smem_bytes;
     const cudaFuncAttribute attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e = cudaFuncSetAttribute(spin_kernel<false, kModeBarrier | kModeProducer>, attr, bytes);
@@ -964,7 +973,11 @@ cudaError_t setup_spin_kernel_attributes(size_t smem_bytes) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(spin_kernel<false, kModeProducer>, attr, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(spin_kernel<false, kModeAll>, attr, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(spin_kernel<true, kModeAll>, attr, bytes);
-    if (e == cudaSuccess) done = smem_bytes;
+    if (e == cudaSuccess) {
+        size_t prev = done_ref.load();
+        while (prev < smem_bytes && !done_ref.compare_exchange_weak(prev, smem_bytes)) {
+        }
+    }
     return e;
 }
 
