@@ -416,7 +416,9 @@ def run_ours(args):
         line["workloads"] = extra
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(c, budget_s=args.cpu_seconds)
+        line["cpu_baseline"]["host"] = _host_cpu()
         line["cpu_dls_baseline"] = cpu_dls_baseline(c)
+        line["cpu_oracle_other_workloads"] = cpu_oracle_other_workloads()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -629,6 +631,39 @@ def cpu_dls_baseline(c, budget_s=3.0):
         oracle.spin_images_omp(pts, nrm, W, B, cs, query_idx=q, rule=rule)
         out[name] = nq / (time.perf_counter() - t0)
     return out
+
+
+def _host_cpu():
+    """Host core count and CPU model (the oracle's timings depend on them)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def cpu_oracle_other_workloads():
+    """The single-thread FP64 oracle on the other single-mesh workloads: every
+    image of the 4,096-point sphere, and 128 of the 1M-point scene's queries."""
+    import oracle
+    from paper_1811_00901_gb300 import workloads as wl
+    res = {}
+    sp = wl.plain_sphere()
+    t0 = time.perf_counter()
+    oracle.spin_images(sp["points"], sp["normals"], sp["W"], sp["bin_size"], sp["cos_s"])
+    res["sphere-4096-W16"] = {"images_per_s": sp["m"] / (time.perf_counter() - t0), "sample": "all 4096 images"}
+    sc = wl.large_scene()
+    q = sc["query_idx"][:128]
+    t0 = time.perf_counter()
+    oracle.spin_images(sc["points"], sc["normals"], sc["W"], sc["bin_size"], sc["cos_s"], query_idx=q)
+    res["scene-1M-W64"] = {"images_per_s": len(q) / (time.perf_counter() - t0),
+                           "sample": "the first 128 of its 262,144 queries (all 1M points each)"}
+    return res
 
 
 def run_reference(args):
