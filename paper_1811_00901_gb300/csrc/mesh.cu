@@ -119,12 +119,15 @@ int grid_blocks(int64_t n) {
     return (int)b;
 }
 
-void free_grid(Grid *g) {
+// Grids and meshes live in the device's stream-ordered pool (its release
+// threshold keeps freed blocks for reuse, so a new mesh of the same size
+// allocates in microseconds); callers free them with no work pending.
+void free_grid(Grid *g, cudaStream_t stream) {
     if (!g) return;
-    cudaFree(g->cell_start);
-    cudaFree(g->pn);
-    cudaFree(g->sorted_pos);
-    cudaFree(g->orig_idx);
+    dev_free(g->cell_start, stream);
+    dev_free(g->pn, stream);
+    dev_free(g->sorted_pos, stream);
+    dev_free(g->orig_idx, stream);
     if (g->ready) cudaEventDestroy(g->ready);
     delete g;
 }
@@ -200,15 +203,17 @@ Grid *mesh_grid(Mesh *m, float cell, cudaStream_t stream, si_status *st) {
         g->dims[k] = dims[k];
     }
     g->ncell = ncell;
-    cudaError_t e;
-    e = cudaMalloc(&g->cell_start, sizeof(int) * (ncell + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&g->pn, sizeof(float4) * 2 * m->n);
-    if (e == cudaSuccess) e = cudaMalloc(&g->sorted_pos, sizeof(int) * m->n);
-    if (e == cudaSuccess) e = cudaMalloc(&g->orig_idx, sizeof(int) * m->n);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ready, cudaEventDisableTiming);
-    if (e != cudaSuccess) {
-        *st = cuda_fail(e, "grid allocation");
-        free_grid(g);
+    cudaError_t e = cudaSuccess;
+    *st = dev_alloc((void **)&g->cell_start, sizeof(int) * (ncell + 1), stream);
+    if (*st == SI_OK) *st = dev_alloc((void **)&g->pn, sizeof(float4) * 2 * m->n, stream);
+    if (*st == SI_OK) *st = dev_alloc((void **)&g->sorted_pos, sizeof(int) * m->n, stream);
+    if (*st == SI_OK) *st = dev_alloc((void **)&g->orig_idx, sizeof(int) * m->n, stream);
+    if (*st == SI_OK) {
+        e = cudaEventCreateWithFlags(&g->ready, cudaEventDisableTiming);
+        if (e != cudaSuccess) *st = cuda_fail(e, "grid event");
+    }
+    if (*st != SI_OK) {
+        free_grid(g, stream);
         return nullptr;
     }
     GridView gv{g->origin[0], g->origin[1], g->origin[2], g->inv_cell, dims[0], dims[1], dims[2]};
@@ -239,7 +244,7 @@ Grid *mesh_grid(Mesh *m, float cell, cudaStream_t stream, si_status *st) {
     if (e != cudaSuccess && *st == SI_OK) *st = cuda_fail(e, "grid build");
     if (*st != SI_OK) {
         cudaStreamSynchronize(stream);
-        free_grid(g);
+        free_grid(g, stream);
         return nullptr;
     }
     m->grids.push_back(g);
@@ -275,10 +280,10 @@ si_status si_mesh_create(const float *points, const float *normals, int64_t n, s
     si_status st = SI_OK;
     cudaError_t e = cudaSuccess;
     do {
-        e = cudaMalloc(&m->pos, sizeof(float4) * n);
-        if (e == cudaSuccess) e = cudaMalloc(&m->nrm, sizeof(float4) * n);
-        if (e == cudaSuccess) e = cudaMalloc(&m->flags, sizeof(unsigned));
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->ready, cudaEventDisableTiming);
+        if ((st = dev_alloc((void **)&m->pos, sizeof(float4) * n, s)) != SI_OK) break;
+        if ((st = dev_alloc((void **)&m->nrm, sizeof(float4) * n, s)) != SI_OK) break;
+        if ((st = dev_alloc((void **)&m->flags, sizeof(unsigned), s)) != SI_OK) break;
+        e = cudaEventCreateWithFlags(&m->ready, cudaEventDisableTiming);
         if (e != cudaSuccess) break;
         e = cudaMemsetAsync(m->flags, 0, sizeof(unsigned), s);
         if (e != cudaSuccess) break;
@@ -318,9 +323,9 @@ si_status si_mesh_create(const float *points, const float *normals, int64_t n, s
     }
     if (st != SI_OK) {
         cudaStreamSynchronize(s);
-        cudaFree(m->pos);
-        cudaFree(m->nrm);
-        cudaFree(m->flags);
+        dev_free(m->pos, s);
+        dev_free(m->nrm, s);
+        dev_free(m->flags, s);
         if (m->ready) cudaEventDestroy(m->ready);
         delete m;
         return st;
@@ -347,14 +352,14 @@ si_status si_mesh_destroy(si_mesh_t mesh) {
     cudaGetDevice(&prev);
     cudaSetDevice(m->device);
     cudaDeviceSynchronize();
-    for (Grid *g : m->grids) free_grid(g);
+    for (Grid *g : m->grids) free_grid(g, nullptr);
     for (auto &pe : m->pending_events) {
         cudaEventDestroy(pe.first);
         cudaEventDestroy(pe.second);
     }
-    cudaFree(m->pos);
-    cudaFree(m->nrm);
-    cudaFree(m->flags);
+    dev_free(m->pos, nullptr);
+    dev_free(m->nrm, nullptr);
+    dev_free(m->flags, nullptr);
     if (m->ready) cudaEventDestroy(m->ready);
     delete m;
     cudaSetDevice(prev);
