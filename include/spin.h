@@ -332,6 +332,16 @@ int64_t si_kernel_launches(void);
  * Synchronises `stream`. */
 si_status si_peak_smem_atomics(int32_t mode, double *atomics_per_s, si_stream stream);
 
+/* Self-check of the bounded device waits (the paper has no counterpart).
+ * Every mbarrier wait of the spin kernel gives up after a time limit, sets the
+ * mesh's timeout flag and lets the kernel return, so that a stalled copy can
+ * never hang the GPU.  This launches a tiny kernel whose blocks wait, with a
+ * limit of limit_ms (1..1000), on an mbarrier that nothing arrives at; on
+ * return *timed_out is 1 when the wait gave up as it must, *waited_ms (may be
+ * NULL) the longest wait seen.  Synchronises `stream`; the context stays
+ * usable. */
+si_status si_check_bounded_wait(int32_t limit_ms, int32_t *timed_out, double *waited_ms, si_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,6 +1,6 @@
 /*
  * spin_oracle_omp.c -- the FP64 oracle's all-pairs spin images, the image
- * loop spread over the host's cores with OpenMP.  TEST AND BASELINE
+ * loop spread over the host's cores with OpenMP.  TEST AND CPU-REFERENCE
  * INFRASTRUCTURE ONLY (bench.py's CPU baseline): it is the shared-memory CPU
  * analogue of the paper's PSIA-STATIC / EPSIA-SS / EPSIA-GSS (Sec. 2.2, 3),
  * the image loop scheduled by OpenMP's schedule(static), schedule(dynamic, 1)

@@ -75,6 +75,8 @@ _SIGNATURES = {
                             ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)],
                            ctypes.c_int),
     "si_candidate_rc2": ([ctypes.c_int32, ctypes.c_float], ctypes.c_float),
+    "si_check_bounded_wait": ([ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                               _P], ctypes.c_int),
     "si_candidate_rc2_binned": ([ctypes.c_int32, ctypes.c_float, ctypes.c_int32], ctypes.c_float),
     "si_get_stats": ([_P, ctypes.POINTER(si_stats)], ctypes.c_int),
     "si_reset_stats": ([_P], ctypes.c_int),
@@ -239,6 +241,14 @@ def si_schedule_chunks(schedule, units, workers):
     _check(load().si_schedule_chunks(ctypes.byref(schedule), int(units), int(workers), buf, cap,
                                      ctypes.byref(nsteps)))
     return list(buf)
+
+
+def si_check_bounded_wait(limit_ms=50, stream=None):
+    """Returns (timed_out, waited_ms) of the bounded-wait self-check."""
+    t = ctypes.c_int32()
+    w = ctypes.c_double()
+    _check(load().si_check_bounded_wait(int(limit_ms), ctypes.byref(t), ctypes.byref(w), _stream_ptr(stream)))
+    return bool(t.value), w.value
 
 
 def si_candidate_rc2(W, bin_size):

@@ -368,3 +368,16 @@ def test_column_edge_pairs_keep_their_whole_weight(W, B):
     got, pr = gpu_run(pts, nrm, W, B, 0.0, query_idx=q, probe=True, schedule=spin.make_schedule("SS"))
     assert got[0].astype(np.int64).sum() == 65536 * int(pr["support"][0])
     compare_with_oracle(got, pts, nrm, W, B, 0.0, q, np.array([0]))
+
+
+def test_bounded_device_wait_gives_up_and_the_context_stays_usable():
+    """The spin kernel's mbarrier waits are bounded: a wait on a barrier that
+    nothing arrives at gives up after its limit and reports it; work launched
+    afterwards runs normally."""
+    import paper_1811_00901_gb300 as spin
+    timed_out, waited = spin.si_check_bounded_wait(50)
+    assert timed_out
+    assert 45.0 <= waited < 5000.0, waited
+    pts, nrm = wl.sphere(1500, 77)
+    got, _ = gpu_run(pts, nrm, 16, 0.05, 0.5)
+    compare_with_oracle(got, pts, nrm, 16, 0.05, 0.5, None, np.arange(0, 1500, 97))
