@@ -189,10 +189,11 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
         p->binning[k] = scheds[k].binning;
         p->modes |= ring_mode(p->log2S[k]) | (scheds[k].binning == SI_BIN_NEAREST ? kModeNearest : 0);
     }
-    p->modes = launch_modes(p->modes, probe);
     p->smem = 0;
     for (int k = 0; k < nitems; ++k)
         if (items[k].m > 0) p->smem = std::max(p->smem, spin_smem_bytes(items[k].W, p->log2S[k]));
+    if (p->smem > (size_t)SI_SMEM_BUDGET_KB * 1024) p->modes |= kModeWide;
+    p->modes = launch_modes(p->modes, probe);
     SI_CUDA(setup_spin_kernel_attributes(p->smem));
     const int per_sm = blocks_per_sm_for(p->smem, p->modes);
     if (per_sm < 1) {

@@ -174,13 +174,18 @@ struct LaunchArgs {
 // warp, larger groups a block barrier per tile.
 constexpr int kModeBarrier = 1, kModeProducer = 2;
 constexpr int kModeNearest = 4;  // some group uses the nearest-bin count (runtime-shape path)
+constexpr int kModeWide = 8;     // the launch's shared memory allows two blocks per SM, not three
 inline int ring_mode(int log2S) { return log2S <= 2 ? kModeProducer : kModeBarrier; }
 // Disciplines compiled into the kernel instance that runs a launch whose
 // groups use `modes`: one discipline alone gets its own instance; mixed
 // launches and probe launches run the instance with both.
+// A mixed launch whose shared memory leaves room for two blocks per SM only
+// (kModeWide) runs a mixed instance built for two blocks, with their registers.
 inline int launch_modes(int modes, bool probe) {
     if (probe || (modes & kModeNearest)) return kModeBarrier | kModeProducer | kModeNearest;
-    return modes == kModeBarrier || modes == kModeProducer ? modes : kModeBarrier | kModeProducer;
+    const int rings = modes & (kModeBarrier | kModeProducer);
+    if (rings == kModeBarrier || rings == kModeProducer) return rings;
+    return (kModeBarrier | kModeProducer) | (modes & kModeWide);
 }
 
 // ---------------------------------------------------------- host helpers --

@@ -754,14 +754,15 @@ __device__ void awf_claim(const LaunchArgs &a, Header &H, const int claim_iter, 
     H.claim = (int)s;
 }
 
-// MODES: the paths compiled in (kModeBarrier | kModeProducer | kModeNearest);
+// MODES: the paths compiled in (kModeBarrier | kModeProducer | kModeNearest),
+// plus kModeWide for a mixed launch that runs two blocks per SM;
 // a launch whose groups all use one discipline runs the instance without the
 // other, whose registers are then allocated for its own loop alone.  Groups
 // in producer mode hold >= 67 KB of images, so at most two blocks fit on an
 // SM: that instance may use the registers of two blocks.
 template <int MODES>
 constexpr int min_blocks_for() {
-    return MODES == kModeProducer ? 2 : SI_MIN_BLOCKS;
+    return MODES == kModeProducer || (MODES & kModeWide) ? 2 : SI_MIN_BLOCKS;
 }
 
 template <bool PROBE, int MODES>
@@ -955,6 +956,7 @@ size_t image_words(int W, int log2S) {
 size_t spin_smem_bytes(int W, int log2S) { return (size_t)shape_smem(W, log2S, tile_for_shape(W, log2S)); }
 
 constexpr int kModeAll = kModeBarrier | kModeProducer | kModeNearest;
+constexpr int kModeMixedWide = kModeBarrier | kModeProducer | kModeWide;
 
 cudaError_t setup_spin_kernel_attributes(size_t smem_bytes) {
     // the attribute belongs to each device's context: remember it per device
@@ -971,6 +973,7 @@ cudaError_t setup_spin_kernel_attributes(size_t smem_bytes) {
     cudaError_t e = cudaFuncSetAttribute(spin_kernel<false, kModeBarrier | kModeProducer>, attr, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(spin_kernel<false, kModeBarrier>, attr, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(spin_kernel<false, kModeProducer>, attr, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(spin_kernel<false, kModeMixedWide>, attr, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(spin_kernel<false, kModeAll>, attr, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(spin_kernel<true, kModeAll>, attr, bytes);
     if (e == cudaSuccess) {
@@ -993,6 +996,9 @@ int blocks_per_sm_for(size_t smem_bytes, int modes) {
     else if (modes == (kModeBarrier | kModeProducer))
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spin_kernel<false, kModeBarrier | kModeProducer>,
                                                           kThreads, smem_bytes);
+    else if (modes == kModeMixedWide)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spin_kernel<false, kModeMixedWide>, kThreads,
+                                                          smem_bytes);
     else
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spin_kernel<false, kModeAll>, kThreads, smem_bytes);
     return e == cudaSuccess ? n : 0;
@@ -1008,6 +1014,8 @@ void launch_spin_kernel(const LaunchArgs &a, int blocks, size_t smem, cudaStream
         spin_kernel<false, kModeProducer><<<blocks, kThreads, smem, stream>>>(a);
     else if (a.modes == (kModeBarrier | kModeProducer))
         spin_kernel<false, kModeBarrier | kModeProducer><<<blocks, kThreads, smem, stream>>>(a);
+    else if (a.modes == kModeMixedWide)
+        spin_kernel<false, kModeMixedWide><<<blocks, kThreads, smem, stream>>>(a);
     else
         spin_kernel<false, kModeAll><<<blocks, kThreads, smem, stream>>>(a);
 }
