@@ -383,9 +383,9 @@ def run_ours(args):
         ex_steps = max(1, min(args.steps, 3))
         extra = {}
         extra["sphere-4096-W16"] = bench_single(spin, torch, dev, wl.plain_sphere(), args.steps, args.warmup, flush,
-                                                stream, kinds=("STATIC", "SS", "GSS", "FAC"))
+                                                stream, kinds=("STATIC", "SS", "GSS", "FAC"), pairs=True)
         extra["scene-1M-W64"] = bench_single(spin, torch, dev, wl.large_scene(), ex_steps, args.warmup, flush,
-                                             stream, kinds=("STATIC", "FAC"))
+                                             stream, kinds=("STATIC", "FAC"), pairs=True)
         # probabilistic factoring with sigma / mu of the group cost measured by
         # the probe run (a group's cost follows its candidate stream length)
         cov = _group_cost_cov(examined_per_image)
@@ -430,7 +430,8 @@ def run_ours(args):
 # the other workloads (secondary keys of the same line)
 # --------------------------------------------------------------------------
 
-def bench_single(spin, torch, dev, c, steps, warmup, flush, stream, kinds=("STATIC", "FAC"), scheds=None):
+def bench_single(spin, torch, dev, c, steps, warmup, flush, stream, kinds=("STATIC", "FAC"), scheds=None,
+                 pairs=False):
     """One mesh, all its images (or its query list), per rule; kernel time by
     events.  ``scheds`` (name -> si_schedule) replaces ``kinds`` when given."""
     n, m, W, B, cs = c["points"].shape[0], c["m"], c["W"], float(c["bin_size"]), float(c["cos_s"])
@@ -462,8 +463,27 @@ def bench_single(spin, torch, dev, c, steps, warmup, flush, stream, kinds=("STAT
                 kms.append(st["kernel_ms"] / max(1, st["kernel_launches"]))
         res[kind] = {"images_per_s": m / (statistics.median(times) / 1e3), "ms_per_step": statistics.median(times),
                      "kernel_ms": statistics.median(kms)}
+    line = {"images": m, "W": W, "points": n, "by_schedule": res}
+    if pairs:
+        # pair counts from one probe run (untimed): the kernel's ALU roofline here
+        mesh = spin.si_mesh_create(tp, tn, n, stream)
+        culled = torch.zeros(m, dtype=torch.int64, device=dev)
+        support = torch.zeros(m, dtype=torch.int64, device=dev)
+        spin.si_generate_probe(mesh, tq, m, W, B, cs, spin.make_schedule("GSS"), out, culled=culled,
+                               support=support, stream=stream)
+        torch.cuda.synchronize()
+        spin.si_get_stats(mesh)
+        spin.si_mesh_destroy(mesh)
+        nc, ns = int(culled.sum().item()), int(support.sum().item())
+        best = min(res, key=lambda k: res[k]["kernel_ms"])
+        peaks, _ = _measured_peaks()
+        alu_peak = sms_count(torch, dev) * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        ops = OPS_PER_CULLED * nc + OPS_PER_SUPPORT * ns
+        line.update(culled_pairs_per_step=nc, support_pairs_per_step=ns,
+                    culled_pairs_per_s=nc / (res[best]["ms_per_step"] / 1e3),
+                    alu_frac=ops / (res[best]["kernel_ms"] / 1e3) / alu_peak, alu_frac_rule=best)
     del out
-    return {"images": m, "W": W, "points": n, "by_schedule": res}
+    return line
 
 
 def bench_batched(spin, torch, dev, steps, warmup, stream):
