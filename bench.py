@@ -404,6 +404,7 @@ def run_ours(args):
         h["over_static"] = {k: v["images_per_s"] / h["by_schedule"]["STATIC"]["images_per_s"]
                             for k, v in h["by_schedule"].items()}
         extra["heterogeneous-heightfield-100k-W32"] = h
+        extra["matching-16k-vs-100k-W32"] = bench_matching(spin, torch, dev, c, ex_steps, args.warmup, stream)
         # Algorithm 1's own nearest-bin count on the bench workload
         extra["nearest-bin-heightfield-100k-W32"] = bench_single(
             spin, torch, dev, c, ex_steps, args.warmup, flush, stream,
@@ -484,6 +485,54 @@ def bench_single(spin, torch, dev, c, steps, warmup, flush, stream, kinds=("STAT
                     alu_frac=ops / (res[best]["kernel_ms"] / 1e3) / alu_peak, alu_frac_rule=best)
     del out
     return line
+
+
+def bench_matching(spin, torch, dev, c, steps, warmup, stream, n_scene=16384, k=5):
+    """Spin-image matching: n_scene images of a rigidly moved copy of the bench
+    mesh against all images of the mesh (correlation over all bins, k best)."""
+    n, m, W, B, cs = c["points"].shape[0], c["m"], c["W"], float(c["bin_size"]), float(c["cos_s"])
+    tp = torch.from_numpy(c["points"]).to(dev)
+    tn = torch.from_numpy(c["normals"]).to(dev)
+    model = torch.empty((m, W, W), dtype=torch.int32, device=dev)
+    mesh = spin.si_mesh_create(tp, tn, n, stream)
+    spin.si_generate(mesh, None, m, W, B, cs, spin.make_schedule("FAC"), model, stream)
+    torch.cuda.synchronize()
+    spin.si_mesh_destroy(mesh)
+    g = torch.Generator().manual_seed(1811009021)
+    rot, _ = torch.linalg.qr(torch.randn(3, 3, generator=g, dtype=torch.float64))
+    rot = rot.to(torch.float32).to(dev)
+    mesh = spin.si_mesh_create((tp @ rot.T + 0.25).contiguous(), (tn @ rot.T).contiguous(), n, stream)
+    q = torch.randperm(m, generator=g)[:n_scene].to(torch.int32).to(dev)
+    scene = torch.empty((n_scene, W, W), dtype=torch.int32, device=dev)
+    spin.si_generate(mesh, q, n_scene, W, B, cs, spin.make_schedule("FAC"), scene, stream)
+    torch.cuda.synchronize()
+    spin.si_mesh_destroy(mesh)
+    idx = torch.empty((n_scene, k), dtype=torch.int32, device=dev)
+    val = torch.empty((n_scene, k), dtype=torch.float32, device=dev)
+    peaks, src = _measured_peaks()
+    res = {}
+    for prec in ("BF16", "FP32"):
+        times = []
+        for it in range(warmup + steps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            spin.si_match(scene, n_scene, model, m, W, k, prec, idx, val, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if it >= warmup:
+                times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        flops = 2.0 * n_scene * m * W * W
+        res[prec] = {"ms": ms, "correlations_per_s": n_scene * m / (ms / 1e3), "tflops": flops / (ms / 1e3) / 1e12}
+        if prec == "BF16" and "bf16_tflops" in peaks:
+            res[prec]["frac_of_bf16_peak"] = res[prec]["tflops"] / float(peaks["bf16_tflops"])
+    # how many scene images found their own point of the unmoved mesh first
+    hit = float((idx[:, 0].long().cpu() == q.long().cpu()).float().mean().item())
+    del model, scene
+    return {"scene_images": n_scene, "model_images": m, "W": W, "k": k, "by_precision": res,
+            "top1_is_the_same_point": hit, "peak_source": src}
 
 
 def bench_batched(spin, torch, dev, steps, warmup, stream):

@@ -332,6 +332,29 @@ int64_t si_kernel_launches(void);
  * Synchronises `stream`. */
 si_status si_peak_smem_atomics(int32_t mode, double *atomics_per_s, si_stream stream);
 
+/* ------------------------------------------------------------- matching --
+ * si_match -- spin-image matching: for each scene image its k best model
+ * images by the linear correlation coefficient over all W x W bins
+ *   R(p, q) = (N sum pq - sum p sum q) / sqrt((N sum p^2 - (sum p)^2)(N sum q^2 - (sum q)^2)),
+ * N = W^2, the similarity measure of spin-image matching (Johnson and Hebert,
+ * 1999, the recognition work the paper cites); an image without variance
+ * correlates 0.  Over all bins R is the dot product of the centred, unit-length
+ * images, so the all-pairs step is one dense contraction, run through cuBLAS
+ * (loaded at first use): SI_MATCH_BF16 on the tensor cores (BF16 operands,
+ * FP32 accumulation: |R error| <= 2^-8 from rounding the unit-length operands
+ * to BF16, plus FP32 accumulation error, about W^2 x 2^-24 at worst),
+ * SI_MATCH_FP32 as an FP32 GEMM (accumulation error only).
+ *   scene : device int32[n_scene][W][W], model : device int32[n_model][W][W]
+ *           (images as si_generate writes them);
+ *   best_idx, best_corr : device [n_scene][k], highest R first, equal values
+ *           by smaller model index; 1 <= k <= min(16, n_model).
+ * Scratch comes from the stream-ordered pool (at most ~1 GiB of correlation
+ * tile plus the centred images).  Stream-ordered; argument errors are
+ * synchronous.  The paper has no counterpart (its subject is generation). */
+typedef enum si_match_precision { SI_MATCH_FP32 = 0, SI_MATCH_BF16 = 1 } si_match_precision;
+si_status si_match(const int32_t *scene, int64_t n_scene, const int32_t *model, int64_t n_model, int32_t W,
+                   int32_t k, int32_t precision, int32_t *best_idx, float *best_corr, si_stream stream);
+
 /* Self-check of the bounded device waits (the paper has no counterpart).
  * Every mbarrier wait of the spin kernel gives up after a time limit, sets the
  * mesh's timeout flag and lets the kernel return, so that a stalled copy can

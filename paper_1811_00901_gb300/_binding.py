@@ -75,6 +75,8 @@ _SIGNATURES = {
                             ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)],
                            ctypes.c_int),
     "si_candidate_rc2": ([ctypes.c_int32, ctypes.c_float], ctypes.c_float),
+    "si_match": ([_P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, _P],
+                 ctypes.c_int),
     "si_check_bounded_wait": ([ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
                                _P], ctypes.c_int),
     "si_candidate_rc2_binned": ([ctypes.c_int32, ctypes.c_float, ctypes.c_int32], ctypes.c_float),
@@ -241,6 +243,17 @@ def si_schedule_chunks(schedule, units, workers):
     _check(load().si_schedule_chunks(ctypes.byref(schedule), int(units), int(workers), buf, cap,
                                      ctypes.byref(nsteps)))
     return list(buf)
+
+
+SI_MATCH_FP32, SI_MATCH_BF16 = 0, 1
+
+
+def si_match(scene, n_scene, model, n_model, W, k, precision, best_idx, best_corr, stream=None):
+    """Each scene image's k best model images by correlation (device buffers)."""
+    if isinstance(precision, str):
+        precision = {"FP32": SI_MATCH_FP32, "BF16": SI_MATCH_BF16}[precision.upper()]
+    _check(load().si_match(_ptr(scene), int(n_scene), _ptr(model), int(n_model), int(W), int(k), int(precision),
+                           _ptr(best_idx), _ptr(best_corr), _stream_ptr(stream)))
 
 
 def si_check_bounded_wait(limit_ms=50, stream=None):
