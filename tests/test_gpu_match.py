@@ -65,10 +65,11 @@ def test_best_matches_against_the_oracle(precision, tol):
         out[idx[i]] = False
         assert r[i, out].max() <= r[i, idx[i, k - 1]] + 2 * tol, i
         assert ref_val[i, k - 1] <= val[i, k - 1] + 2 * tol
-        # where the oracle's list is separated by more than the bound, the lists agree
-        gaps = np.diff(np.concatenate([ref_val[i], [match.correlations(scene[i:i + 1], model)[0].min() - 1]]))
+        # where the oracle's ranking is separated by more than the bound on both
+        # sides of a place, the lists agree at that place
+        sv = np.sort(r[i])[::-1]
         for t in range(k):
-            if -gaps[t] > 2 * tol and (t == 0 or -gaps[t - 1] > 2 * tol):
+            if sv[t] - sv[t + 1] > 2 * tol and (t == 0 or sv[t - 1] - sv[t] > 2 * tol):
                 assert idx[i, t] == ref_idx[i, t], (i, t)
     # the constant image correlates 0 with everything
     assert np.all(val[-1] == 0.0)
