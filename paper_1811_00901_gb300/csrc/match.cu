@@ -114,50 +114,114 @@ __device__ __forceinline__ bool better(float va, int ia, float vb, int ib) {
     return va > vb || (va == vb && ia < ib);
 }
 
-// One warp per scene row of the correlation tile: each lane keeps its k best
-// (sorted, in registers), then the warp merges them k times by a warp arg-max.
-template <int KMAX>
-__global__ void topk_kernel(const float *__restrict__ C, int rows, int cols, int k, int64_t row0,
-                            int32_t *__restrict__ best_idx, float *__restrict__ best_val) {
-    const int lane = threadIdx.x & 31;
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
-        const float *c = C + (int64_t)r * cols;
-        float v[KMAX];
-        int ix[KMAX];
-#pragma unroll
-        for (int t = 0; t < KMAX; ++t) {
-            v[t] = -INFINITY;
-            ix[t] = INT_MAX;
+// A thread's k best so far, highest first (kept in local memory: insertions
+// are rare once the list holds high values).
+struct TopList {
+    float v[16];
+    int ix[16];
+};
+
+// Inserts (x, xi) into a sorted list of k, dropping the last; returns the new k-th.
+__device__ __noinline__ void topk_insert(TopList &t, const int k, float x, int xi, float &thr_v, int &thr_i) {
+    for (int q = 0; q < k; ++q) {
+        if (better(x, xi, t.v[q], t.ix[q])) {
+            const float tv = t.v[q];
+            const int ti = t.ix[q];
+            t.v[q] = x;
+            t.ix[q] = xi;
+            x = tv;
+            xi = ti;
         }
-        for (int j = lane; j < cols; j += 32) {
-            float x = c[j];
-            int xi = j;
-            // insert (x, xi) into the sorted list, dropping the last
+    }
+    thr_v = t.v[k - 1];
+    thr_i = t.ix[k - 1];
+}
+
+// One block per scene row of the correlation tile.  Each thread scans its
+// strided share with eight loads in flight, offering a value to its list only
+// when it beats the list's k-th; then each warp merges its 32 lists by k warp
+// arg-max rounds, and thread 0 picks the k best of the warps' lists.
+constexpr int kTopThreads = 256;
+
+__global__ void __launch_bounds__(kTopThreads) topk_kernel(const float *__restrict__ C, int rows, int cols, int k,
+                                                            int64_t row0, int32_t *__restrict__ best_idx,
+                                                            float *__restrict__ best_val) {
+    __shared__ float sv[kTopThreads / 32][16];
+    __shared__ int si_[kTopThreads / 32][16];
+    __shared__ float mv[kTopThreads];
+    __shared__ int mi[kTopThreads];
+    __shared__ float tv_s;
+    __shared__ int ti_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kU = 8;
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const float *c = C + (int64_t)r * cols;
+        // pass 1: each thread's best; the k-th best of these 256 bounds the
+        // row's k-th best from below, so nothing worse can make the list
+        float bv = -INFINITY;
+        int bi = INT_MAX;
+        {
+            int j0 = threadIdx.x;
+            for (; j0 + kTopThreads * (kU - 1) < cols; j0 += kTopThreads * kU) {
+                float x[kU];
 #pragma unroll
-            for (int t = 0; t < KMAX; ++t) {
-                if (t < k && better(x, xi, v[t], ix[t])) {
-                    const float tv = v[t];
-                    const int ti = ix[t];
-                    v[t] = x;
-                    ix[t] = xi;
-                    x = tv;
-                    xi = ti;
+                for (int u = 0; u < kU; ++u) x[u] = c[j0 + kTopThreads * u];
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+                    if (better(x[u], j0 + kTopThreads * u, bv, bi)) {
+                        bv = x[u];
+                        bi = j0 + kTopThreads * u;
+                    }
+            }
+            for (int j = j0; j < cols; j += kTopThreads) {
+                const float x = c[j];
+                if (better(x, j, bv, bi)) {
+                    bv = x;
+                    bi = j;
                 }
             }
         }
-        int head = 0;
-        for (int t = 0; t < k; ++t) {
-            float hv = -INFINITY;
-            int hi = INT_MAX;
+        mv[threadIdx.x] = bv;
+        mi[threadIdx.x] = bi;
+        __syncthreads();
+        int rank = 0;
+        for (int o = 0; o < kTopThreads; ++o) rank += better(mv[o], mi[o], bv, bi) ? 1 : 0;
+        if (rank == k - 1) {  // ranks of distinct (value, index) pairs are distinct
+            tv_s = bv;
+            ti_s = bi;
+        }
+        __syncthreads();
+        // pass 2: lists of the values not worse than that bound
+        TopList t;
+        for (int q = 0; q < k; ++q) {
+            t.v[q] = -INFINITY;
+            t.ix[q] = INT_MAX;
+        }
+        const float bound_v = tv_s;
+        const int bound_i = ti_s;
+        float thr_v = -INFINITY;
+        int thr_i = INT_MAX;
+        auto wanted = [&](float x, int j) {
+            return !better(bound_v, bound_i, x, j) && better(x, j, thr_v, thr_i);
+        };
+        int j0 = threadIdx.x;
+        for (; j0 + kTopThreads * (kU - 1) < cols; j0 += kTopThreads * kU) {
+            float x[kU];
 #pragma unroll
-            for (int q = 0; q < KMAX; ++q)
-                if (q == head) {
-                    hv = v[q];
-                    hi = ix[q];
-                }
-            float bv = hv;
-            int bi = hi, bl = lane;
+            for (int u = 0; u < kU; ++u) x[u] = __ldcs(c + j0 + kTopThreads * u);
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (wanted(x[u], j0 + kTopThreads * u)) topk_insert(t, k, x[u], j0 + kTopThreads * u, thr_v, thr_i);
+        }
+        for (int j = j0; j < cols; j += kTopThreads) {
+            const float x = __ldcs(c + j);
+            if (wanted(x, j)) topk_insert(t, k, x, j, thr_v, thr_i);
+        }
+        // warp merge: k rounds of arg-max over the lanes' list heads
+        int head = 0;
+        for (int q = 0; q < k; ++q) {
+            float bv = head < k ? t.v[head] : -INFINITY;
+            int bi = head < k ? t.ix[head] : INT_MAX, bl = lane;
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) {
                 const float ov = __shfl_xor_sync(0xffffffffu, bv, d);
@@ -171,10 +235,26 @@ __global__ void topk_kernel(const float *__restrict__ C, int rows, int cols, int
             }
             if (lane == bl) ++head;
             if (lane == 0) {
-                best_idx[(row0 + r) * k + t] = bi == INT_MAX ? -1 : bi;
-                best_val[(row0 + r) * k + t] = bv;
+                sv[warp][q] = bv;
+                si_[warp][q] = bi;
             }
         }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int hw[kTopThreads / 32] = {};
+            for (int q = 0; q < k; ++q) {
+                // k picks from 8 lists of k: some list always has an entry left
+                int bw = -1;
+                for (int w = 0; w < kTopThreads / 32; ++w) {
+                    if (hw[w] >= k) continue;
+                    if (bw < 0 || better(sv[w][hw[w]], si_[w][hw[w]], sv[bw][hw[bw]], si_[bw][hw[bw]])) bw = w;
+                }
+                best_val[(row0 + r) * k + q] = sv[bw][hw[bw]];
+                best_idx[(row0 + r) * k + q] = si_[bw][hw[bw]] == INT_MAX ? -1 : si_[bw][hw[bw]];
+                ++hw[bw];
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -250,7 +330,7 @@ extern "C" si_status si_match(const int32_t *scene, int64_t n_scene, const int32
             break;
         }
         note_launches(1);
-        topk_kernel<kMatchMaxK><<<(nr + 7) / 8, 256, 0, st>>>(ct, nr, (int)n_model, k, r0, best_idx, best_corr);
+        topk_kernel<<<nr, kTopThreads, 0, st>>>(ct, nr, (int)n_model, k, r0, best_idx, best_corr);
         note_launches(1);
         e = cudaGetLastError();
     }
