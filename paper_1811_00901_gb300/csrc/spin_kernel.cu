@@ -282,7 +282,7 @@ __device__ __forceinline__ void trip(const float4 *p0, const float4 *p1, const b
     }
 }
 
-// Whether a full tile (kTile candidates) of this shape takes a path without
+// Whether a full tile (TN candidates) of this shape takes a path without
 // per-lane range checks: compile-time shapes only.
 template <int WT, int LS, int NCONS, int TN>
 constexpr bool has_full_path() {
