@@ -273,7 +273,6 @@ def run_ours(args):
 
     results = {}
     clocks = ClockSampler(local)
-    launches0 = spin.si_kernel_launches()
     timed_launches = 0
     kernel_ms = {}
     clocks.start()
@@ -312,7 +311,6 @@ def run_ours(args):
                          "setup_ms": statistics.median([t - k for t, k in zip(times, kms)])}
         kernel_ms[name] = statistics.median(kms)
     clk = clocks.stop()
-    del launches0
 
     dls = ["SS", "GSS", "FAC"] + (["tuned"] if tuned_desc["kind"] != "STATIC" else [])
     best = max(dls, key=lambda k: results[k]["images_per_s"])
@@ -342,8 +340,7 @@ def run_ours(args):
     # ---- roofline of the spin kernel (the dominant kernel)
     peaks, peak_src = _measured_peaks()
     f_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    import torch as _t
-    sms = _t.cuda.get_device_properties(dev).multi_processor_count
+    sms = sms_count(torch, dev)
     alu_peak = sms * 128 * f_mhz * 1e6  # lane-ops/s at the maximum SM clock
     ops = OPS_PER_CULLED * n_culled + OPS_PER_SUPPORT * n_support
     k_ms = kernel_ms[best]
