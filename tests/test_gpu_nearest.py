@@ -36,7 +36,7 @@ def test_sphere_every_image_bit_exact():
     np.testing.assert_array_equal(pr["support"], sup)
 
 
-@pytest.mark.parametrize("W,B", [(32, 0.01), (5, 0.04), (7, 0.03), (2, 0.1), (127, 0.002)])
+@pytest.mark.parametrize("W,B", [(32, 0.01), (5, 0.04), (7, 0.03), (2, 0.1), (127, 0.002), (128, 0.002)])
 def test_heightfield_sampled_images_bit_exact(W, B):
     import paper_1811_00901_gb300 as spin
     pts, nrm = wl.heightfield(6000, 21)

@@ -74,9 +74,11 @@ def test_object_scene_w64_query_list():
     np.testing.assert_array_equal(imgs[10], imgs[11])
 
 
-@pytest.mark.parametrize("W,B,deg", [(2, 0.1, 180.0), (5, 0.1, 180.0), (7, 0.07, 45.0), (127, 0.004, 60.0)])
+@pytest.mark.parametrize("W,B,deg", [(2, 0.1, 180.0), (5, 0.1, 180.0), (7, 0.07, 45.0), (127, 0.004, 60.0),
+                                     (128, 0.004, 60.0)])
 def test_odd_widths(W, B, deg):
-    """The paper's own W = 5 (Sec. 4.1) and other widths, including the extremes."""
+    """The paper's own W = 5 (Sec. 4.1) and other widths, including the extremes
+    (W = 128 is the largest the library takes)."""
     pts, nrm = wl.object_scene(3000, 8, n_objects=6)
     c = wl.cos_deg(deg)
     imgs, pr = gpu_run(pts, nrm, W, B, c, query_idx=np.arange(0, 3000, 7).astype(np.int32), probe=True)
@@ -381,3 +383,16 @@ def test_bounded_device_wait_gives_up_and_the_context_stays_usable():
     pts, nrm = wl.sphere(1500, 77)
     got, _ = gpu_run(pts, nrm, 16, 0.05, 0.5)
     compare_with_oracle(got, pts, nrm, 16, 0.05, 0.5, None, np.arange(0, 1500, 97))
+
+
+@pytest.mark.parametrize("group", [0, 1, 2])
+def test_widest_images_with_every_group_that_fits(group):
+    """W = 128 (the maximum): a group of one image needs ~100 KB of shared memory,
+    two need ~166 KB; both run, and agree with each other and the oracle."""
+    import paper_1811_00901_gb300 as spin
+    pts, nrm = wl.heightfield(4000, 33)
+    W, B, c = 128, 0.002, 0.5
+    q = np.arange(0, 4000, 37).astype(np.int32)
+    imgs, pr = gpu_run(pts, nrm, W, B, c, query_idx=q, probe=True,
+                       schedule=spin.make_schedule("SS", group=group))
+    compare_with_oracle(imgs, pts, nrm, W, B, c, q, np.arange(len(q)), support=pr["support"])
