@@ -11,7 +11,8 @@
  * Each contributing X adds weight 1, split bilinearly over the four corners.
  *
  * Output format (every entry point): int32 out[m][W][W], row-major, row i =
- * u bin, column j = v bin, value = weight x 65536 (16 fractional bits).  The
+ * u bin, column j = v bin, value = weight x 65536 (16 fractional bits; with
+ * SI_BIN_NEAREST, Algorithm 1's own count, the value is the count).  The
  * coordinates are quantised as U = rn(u * 65536), V = rn(v * 65536) (round to
  * nearest even); with A = U mod 65536, Bq = V mod 65536, i = U >> 16,
  * j = V >> 16 the corner weights are
@@ -23,7 +24,8 @@
  *
  * Image loop scheduling (Sec. 2.2 and Algorithm 3): the loop over images is
  * run by persistent thread blocks ("workers") that take chunks of the loop
- * under STATIC, SS, GSS or FAC.  The scheduled iteration is one image GROUP:
+ * under STATIC, SS, GSS or FAC (and FAC_PROB, AWF).  The scheduled iteration
+ * is one image GROUP:
  * `group` consecutive images (in grid order) that a worker generates together
  * against one shared stream of candidate points.
  *
