@@ -24,19 +24,20 @@ si_status cuda_fail(cudaError_t e, const char *what);
     } while (0)
 
 // ------------------------------------------------------------- constants --
-// Build-time shape of the spin kernel (defaults measured best on GB300).
+// Build-time shape of the spin kernel (defaults measured best on GB300):
+// 12-warp blocks, two per SM, up to 113 KB of shared memory each.
 #ifndef SI_THREADS
-#define SI_THREADS 256
+#define SI_THREADS 384
 #endif
 #ifndef SI_MIN_BLOCKS
-#define SI_MIN_BLOCKS 3
+#define SI_MIN_BLOCKS 2
 #endif
 #ifndef SI_SMEM_BUDGET_KB
-#define SI_SMEM_BUDGET_KB 75
+#define SI_SMEM_BUDGET_KB 113
 #endif
 constexpr int kThreads = SI_THREADS;  // threads per spin-kernel block
 #ifndef SI_TILE_MAX
-#define SI_TILE_MAX 512
+#define SI_TILE_MAX 576
 #endif
 #ifndef SI_TILE_MIN
 #define SI_TILE_MIN 448
@@ -174,7 +175,7 @@ struct LaunchArgs {
 // warp, larger groups a block barrier per tile.
 constexpr int kModeBarrier = 1, kModeProducer = 2;
 constexpr int kModeNearest = 4;  // some group uses the nearest-bin count (runtime-shape path)
-constexpr int kModeWide = 8;     // the launch's shared memory allows two blocks per SM, not three
+constexpr int kModeWide = 8;     // the launch's shared memory allows fewer blocks per SM than SI_MIN_BLOCKS
 inline int ring_mode(int log2S) { return log2S <= 2 ? kModeProducer : kModeBarrier; }
 // Disciplines compiled into the kernel instance that runs a launch whose
 // groups use `modes`: one discipline alone gets its own instance; mixed

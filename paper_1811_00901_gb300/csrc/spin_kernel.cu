@@ -100,9 +100,9 @@ constexpr int shape_smem(int W, int log2S, int tn) {
 }
 
 // Candidates per tile for a group shape.  Producer-ring shapes (<= 4 images)
-// run two blocks per SM and take kTileMax.  Block-barrier shapes take the
-// largest tile, a whole number of unrolled trips (2 x 8 warps x 32/S
-// candidates), that keeps three blocks per SM, else kTileMax.
+// take kTileMax.  Block-barrier shapes take the largest tile, a whole number
+// of unrolled trips (2 x kWarps x 32/S candidates), that keeps SI_MIN_BLOCKS
+// blocks per SM, else kTileMax.
 constexpr int tile_for_shape(int W, int log2S) {
     if (log2S <= 2) return kTileMax;
     const int unit = 2 * kWarps * (32 >> log2S);
@@ -816,11 +816,11 @@ __global__ void __launch_bounds__(kThreads, min_blocks_for<MODES>()) spin_kernel
         const int key = it.W * 8 + it.log2S;
         for (int u = u0; u < u1 && alive; ++u) {
             // specialised shapes for the common widths, a runtime one otherwise
-            // (the nearest-bin count: W = 32 in groups of 8, else the runtime shape)
+            // (the nearest-bin count: W = 32 in groups of 16, else the runtime shape)
             if ((MODES & kModeNearest) != 0 && it.binning == SI_BIN_NEAREST) {
                 if constexpr ((MODES & kModeNearest) != 0) {
-                    if (key == 32 * 8 + 3)
-                        alive = process_group<32, 3, PROBE, false, true>(it, u, step, sv, phase_bits);
+                    if (key == 32 * 8 + 4)
+                        alive = process_group<32, 4, PROBE, false, true>(it, u, step, sv, phase_bits);
                     else if (it.log2S <= 2)
                         alive = process_group<0, 0, PROBE, true, true>(it, u, step, sv, phase_bits);
                     else
@@ -1035,8 +1035,8 @@ int choose_log2_group(int W, int requested_group) {
             l = c;
             break;
         }
-    // wide images: when three blocks per SM leave at most two images per
-    // group, four images at two blocks per SM feed each tile better
+    // wide images: when the budget leaves at most two images per group, four
+    // images at two blocks per SM feed each tile better
     if (l <= 1 && spin_smem_bytes(W, l + 1) <= (size_t)113 * 1024) ++l;
     return l;
 }
