@@ -662,24 +662,45 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
         return false;
     }
     __syncthreads();
-    // ---- write-out: pixel (i, j) of slot q lives at ((i*(W+1) + j) * S + q)
+    // ---- write-out: pixel (i, j) of slot q lives at ((i*(W+1) + j) * S + q).
+    // A thread moves up to four images of one pixel with one shared read; the
+    // threads of a warp take consecutive quads of a pixel, then consecutive
+    // pixels, so the shared reads stay conflict-free and each warp store
+    // writes whole 32-byte sectors of 32 / (S/4) pixels per image (a partial
+    // sector costs a transfer of its own when the output is host memory).
     long long pix = 0;
     const int npix = W * W;
     int32_t *__restrict__ out = it.out;
-    for (int e = tid; e < (npix << sh.log2S()); e += kThreads) {
-        const int q = e & (S - 1);
-        if (q >= nq) continue;
-        const int p = e >> sh.log2S();
+    const int lv = sh.log2S() < 2 ? sh.log2S() : 2;  // log2 of the images per read
+    const int lq = sh.log2S() - lv;                   // log2 of the reads per pixel
+    const int nvq = (nq + (1 << lv) - 1) >> lv;       // reads per pixel that hold live images
+    for (int e = tid; e < (npix << lq); e += kThreads) {
+        const int c = e & ((1 << lq) - 1);
+        if (c >= nvq) continue;
+        const int p = e >> lq;
         const int i = p / W, j = p - i * W;
-        const int v = img[(i * W1 + j) * S + q];
-        const int qs = Q[q].slot;
-        if (qs >= 0) {
-            if (K == 1)
-                __stcs(out + (int64_t)qs * npix + p, v);
-            else if (v != 0)
-                atomicAdd(out + (int64_t)qs * npix + p, v);  // partial image of one slice
+        const int *src = img + (i * W1 + j) * S + (c << lv);
+        int v[4];
+        if (lv == 2) {
+            const int4 x = *reinterpret_cast<const int4 *>(src);
+            v[0] = x.x, v[1] = x.y, v[2] = x.z, v[3] = x.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = k < (1 << lv) ? src[k] : 0;
         }
-        pix += v;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int q = (c << lv) + k;
+            if (k >= (1 << lv) || q >= nq) continue;
+            const int qs = Q[q].slot;
+            if (qs >= 0) {
+                if (K == 1)
+                    __stcs(out + (int64_t)qs * npix + p, v[k]);
+                else if (v[k] != 0)
+                    atomicAdd(out + (int64_t)qs * npix + p, v[k]);  // partial image of one slice
+            }
+            pix += v[k];
+        }
     }
     if (K > 1) {
         // contributing pairs per image, summed over slices for the exact
