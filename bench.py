@@ -395,8 +395,8 @@ def run_ours(args):
                 "FAC_PROB": spin.make_schedule("FAC_PROB", fac_cov=cov, **shape),
                 "AWF": spin.make_schedule("AWF", **shape)}), fac_cov=cov)
         # heterogeneity emulation (Sec. 5.2's Type2 + Type1 runs): the first half
-        # of the workers 3x slower, and they request first
-        P = sms_count(torch, dev) * 3
+        # of the resident workers 3x slower, and they request first
+        P = spin.si_default_workers(c["W"], spin.make_schedule("FAC", **shape))
         het = {k: spin.make_schedule(k, num_workers=P, slow_workers=P // 2, slowdown=3.0, fac_cov=cov, **shape)
                for k in ("STATIC", "SS", "GSS", "FAC", "FAC_PROB", "AWF")}
         h = bench_single(spin, torch, dev, c, ex_steps, args.warmup, flush, stream, scheds=het)

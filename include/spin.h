@@ -178,6 +178,17 @@ si_status si_mesh_destroy(si_mesh_t mesh);
 si_status si_mesh_prepare(si_mesh_t mesh, int32_t W, float bin_size,
                           const si_schedule *schedule, si_stream stream);
 
+/* si_default_workers -- the worker count P that num_workers = 0 gives a
+ * single-item call of width W with `schedule`'s group and binning on the
+ * current device: SMs x spin-kernel blocks resident per SM.  All P workers
+ * run at once; a larger num_workers launches blocks that start only when
+ * others have finished (Sec. 4's P processing elements are the resident
+ * ones).  `schedule` may be NULL (defaults).
+ *   workers : host int32, written on SI_OK.
+ * SI_ERR_INVALID for W outside [2, 128], a bad group, or a shape that needs
+ * more shared memory than a block has; SI_ERR_CUDA if the device query fails. */
+si_status si_default_workers(int32_t W, const si_schedule *schedule, int32_t *workers);
+
 /* -------------------------------------------------------------- generate --
  * si_generate -- spin images of m query points (Algorithm 1; the image range
  * of Algorithm 2 is the chunk a worker receives).

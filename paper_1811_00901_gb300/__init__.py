@@ -9,7 +9,7 @@ from ._binding import (  # noqa: F401
     SI_SCHED_AWF, SI_SCHED_FAC, SI_SCHED_FAC_PROB, SI_SCHED_GSS, SI_SCHED_SS, SI_SCHED_STATIC, SI_BIN_BILINEAR, SI_BIN_NEAREST,
     BIN_NAMES, SpinError, batch_items, exported_names, load,
     make_schedule, si_candidate_rc2, si_candidate_rc2_binned, si_check_bounded_wait, si_match, SI_MATCH_FP32,
-    SI_MATCH_BF16, si_chunk_table, si_schedule_chunks, si_generate, si_generate_batched, si_generate_host,
+    SI_MATCH_BF16, si_chunk_table, si_schedule_chunks, si_default_workers, si_generate, si_generate_batched, si_generate_host,
     si_generate_noalloc, si_generate_probe, si_get_stats, si_last_error, si_mesh_create, si_mesh_destroy, si_mesh_prepare,
     si_reset_stats, si_serve_add_mesh, si_serve_create, si_serve_destroy, si_serve_poll, si_serve_release,
     si_serve_result, si_serve_submit, si_serve_wait, si_set_timing, si_tune_clear, si_tune_load, si_tune_lookup,

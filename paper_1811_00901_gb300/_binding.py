@@ -58,6 +58,7 @@ _SIGNATURES = {
     "si_mesh_create": ([_P, _P, ctypes.c_int64, _P, ctypes.POINTER(_P)], ctypes.c_int),
     "si_mesh_destroy": ([_P], ctypes.c_int),
     "si_mesh_prepare": ([_P, ctypes.c_int32, ctypes.c_float, ctypes.POINTER(si_schedule), _P], ctypes.c_int),
+    "si_default_workers": ([ctypes.c_int32, ctypes.POINTER(si_schedule), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "si_generate": ([_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_float, si_schedule, _P, _P],
                     ctypes.c_int),
     "si_generate_probe": ([_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_float, si_schedule,
@@ -181,6 +182,15 @@ def si_mesh_destroy(mesh):
 def si_mesh_prepare(mesh, W, bin_size, schedule=None, stream=None):
     sp = ctypes.byref(schedule) if schedule is not None else None
     _check(load().si_mesh_prepare(mesh, int(W), float(bin_size), sp, _stream_ptr(stream)))
+
+
+def si_default_workers(W, schedule=None):
+    """Resident workers (SMs x spin-kernel blocks per SM) of a call of width
+    W with the schedule's group and binning on the current device."""
+    sp = ctypes.byref(schedule) if schedule is not None else None
+    v = ctypes.c_int32(0)
+    _check(load().si_default_workers(int(W), sp, ctypes.byref(v)))
+    return int(v.value)
 
 
 def si_generate(mesh, query_idx, m, W, bin_size, cos_s, schedule, out, stream=None):

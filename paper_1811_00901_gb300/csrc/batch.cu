@@ -192,8 +192,7 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
     p->smem = 0;
     for (int k = 0; k < nitems; ++k)
         if (items[k].m > 0) p->smem = std::max(p->smem, spin_smem_bytes(items[k].W, p->log2S[k]));
-    if (p->smem > (size_t)SI_SMEM_BUDGET_KB * 1024) p->modes |= kModeWide;
-    p->modes = launch_modes(p->modes, probe);
+    p->modes = launch_modes_for(p->modes, p->smem, probe);
     SI_CUDA(setup_spin_kernel_attributes(p->smem));
     const int per_sm = blocks_per_sm_for(p->smem, p->modes);
     if (per_sm < 1) {

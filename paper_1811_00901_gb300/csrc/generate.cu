@@ -137,6 +137,33 @@ si_status si_mesh_prepare(si_mesh_t mesh, int32_t W, float bin_size, const si_sc
     return SI_OK;
 }
 
+si_status si_default_workers(int32_t W, const si_schedule *schedule, int32_t *workers) {
+    const int group = schedule ? schedule->group : 0;
+    const int binning = schedule ? schedule->binning : SI_BIN_BILINEAR;
+    if (!workers || W < 2 || W > kMaxW || !valid_group(group) ||
+        (binning != SI_BIN_BILINEAR && binning != SI_BIN_NEAREST)) {
+        set_error("si_default_workers: bad arguments");
+        return SI_ERR_INVALID;
+    }
+    const int l2 = choose_log2_group(W, group);
+    const size_t smem = spin_smem_bytes(W, l2);
+    if (smem > (size_t)227 * 1024) {
+        set_error("W = %d with group %d needs more shared memory than a block has", W, 1 << l2);
+        return SI_ERR_INVALID;
+    }
+    int dev = 0;
+    SI_CUDA(cudaGetDevice(&dev));
+    const int modes = launch_modes_for(ring_mode(l2) | (binning == SI_BIN_NEAREST ? kModeNearest : 0), smem, false);
+    SI_CUDA(setup_spin_kernel_attributes(smem));
+    const int per_sm = blocks_per_sm_for(smem, modes);
+    if (per_sm < 1) {
+        set_error("spin kernel does not fit on an SM with %zu bytes of shared memory", smem);
+        return SI_ERR_INVALID;
+    }
+    *workers = num_sms(dev) * per_sm;
+    return SI_OK;
+}
+
 si_status si_generate_host(const float *points, const float *normals, int64_t n, const int32_t *query_idx,
                            int64_t m, int32_t W, float bin_size, float cos_support_angle, si_schedule schedule,
                            int32_t *out, si_stream stream) {

@@ -188,6 +188,12 @@ inline int launch_modes(int modes, bool probe) {
     if (rings == kModeBarrier || rings == kModeProducer) return rings;
     return (kModeBarrier | kModeProducer) | (modes & kModeWide);
 }
+// The same from the groups' own modes (ring_mode, kModeNearest) and the
+// launch's dynamic shared memory.
+inline int launch_modes_for(int modes, size_t smem_bytes, bool probe) {
+    if (smem_bytes > (size_t)SI_SMEM_BUDGET_KB * 1024) modes |= kModeWide;
+    return launch_modes(modes, probe);
+}
 
 // ---------------------------------------------------------- host helpers --
 // Column support threshold: v = alpha / B < W - 1  <=>  alpha^2 < ((W-1) B)^2.

@@ -135,3 +135,12 @@ def test_tuning_table_json_round_trip(lib, tmp_path):
                    '"num_workers": 0, "group": 1, "grid_div": 1}]}')
     with pytest.raises(spin.SpinError):
         spin.si_tune_load(str(bad))
+
+
+@pytest.mark.parametrize("W,group,binning", [(1, 0, 0), (129, 0, 0), (32, 3, 0), (32, 0, 7)])
+def test_default_workers_rejects_bad_arguments(W, group, binning):
+    """Argument checks come before any device query, so they hold without a GPU."""
+    import paper_1811_00901_gb300 as spin
+    with pytest.raises(spin.SpinError) as e:
+        spin.si_default_workers(W, spin.make_schedule("FAC", group=group, binning=binning))
+    assert e.value.status == spin.SI_ERR_INVALID

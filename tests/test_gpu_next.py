@@ -63,6 +63,26 @@ def test_slow_workers_change_no_image_and_take_the_first_steps(kind):
     np.testing.assert_array_equal(pr["worker"][first], pr["step"][first])
 
 
+def test_default_workers_match_the_default_launch():
+    """si_default_workers is SMs x resident blocks; STATIC with num_workers = 0
+    runs one step per worker.  The nearest-bin count runs the kernel instance
+    that probe launches run, so the probe's step count is that number."""
+    import torch
+
+    import paper_1811_00901_gb300 as spin
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for W in (8, 16, 32, 64, 128):
+        P = spin.si_default_workers(W)
+        assert P % sms == 0 and 1 <= P // sms <= 2048 // 32, (W, P)
+    W = 16
+    sched = spin.make_schedule("STATIC", binning="NEAREST")
+    P = spin.si_default_workers(W, sched)
+    pts, nrm = wl.heightfield(40_000, 5)
+    _, pr = gpu_run(pts, nrm, W, 0.02, 0.5, probe=True, schedule=sched)
+    assert int(pr["step"].max()) + 1 == P
+    assert len(np.unique(pr["worker"])) == P
+
+
 def test_slow_workers_slow_static_down_more_than_self_scheduling():
     """Half the workers 6x slower: STATIC (equal blocks) takes several times as
     long; SS moves the work to the fast workers."""
@@ -89,7 +109,7 @@ def test_slow_workers_slow_static_down_more_than_self_scheduling():
         return st["kernel_ms"] / st["kernel_launches"]
 
     try:
-        P = 152 * 3
+        P = spin.si_default_workers(W)
         hom = kernel_ms(spin.make_schedule("STATIC", num_workers=P))
         het_static = kernel_ms(spin.make_schedule("STATIC", num_workers=P, slow_workers=P // 2, slowdown=6.0))
         het_ss = kernel_ms(spin.make_schedule("SS", num_workers=P, slow_workers=P // 2, slowdown=6.0))
@@ -167,7 +187,7 @@ def test_awf_balances_slow_workers():
         return st["kernel_ms"] / st["kernel_launches"]
 
     try:
-        P = 152 * 3
+        P = spin.si_default_workers(W)
         static = kernel_ms(spin.make_schedule("STATIC", num_workers=P, slow_workers=P // 2, slowdown=4.0))
         fac = kernel_ms(spin.make_schedule("FAC", num_workers=P, slow_workers=P // 2, slowdown=4.0))
         awf = kernel_ms(spin.make_schedule("AWF", num_workers=P, slow_workers=P // 2, slowdown=4.0))
