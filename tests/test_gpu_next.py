@@ -164,33 +164,35 @@ def test_awf_batched_items_share_one_loop():
 def test_awf_balances_slow_workers():
     """With half the workers 4x slower, AWF moves work to the fast workers: it
     finishes well before STATIC (which waits for the slow workers' equal
-    blocks) and close to FAC."""
+    blocks) and close to FAC.  Both start with FAC2's first batch, which at a
+    4x slowdown already sets the makespan near half of STATIC's once chunks
+    are fine (here about 25 groups per worker)."""
     import torch
 
     import paper_1811_00901_gb300 as spin
-    pts, nrm = wl.heightfield(30_000, 14)
+    pts, nrm = wl.heightfield(60_000, 14)
     W, B, c = 32, 0.01, wl.cos_deg(60.0)
     dev = torch.device("cuda:0")
     mesh = spin.si_mesh_create(torch.from_numpy(pts).to(dev), torch.from_numpy(nrm).to(dev))
-    out = torch.empty((30_000, W, W), dtype=torch.int32, device=dev)
+    out = torch.empty((60_000, W, W), dtype=torch.int32, device=dev)
 
     def kernel_ms(sched):
-        spin.si_generate(mesh, None, 30_000, W, B, c, sched, out)
+        spin.si_generate(mesh, None, 60_000, W, B, c, sched, out)
         torch.cuda.synchronize()
         spin.si_reset_stats(mesh)
         spin.si_set_timing(True)
         for _ in range(3):
-            spin.si_generate(mesh, None, 30_000, W, B, c, sched, out)
+            spin.si_generate(mesh, None, 60_000, W, B, c, sched, out)
         torch.cuda.synchronize()
         st, _ = spin.si_get_stats(mesh)
         spin.si_set_timing(False)
         return st["kernel_ms"] / st["kernel_launches"]
 
     try:
-        P = spin.si_default_workers(W)
-        static = kernel_ms(spin.make_schedule("STATIC", num_workers=P, slow_workers=P // 2, slowdown=4.0))
-        fac = kernel_ms(spin.make_schedule("FAC", num_workers=P, slow_workers=P // 2, slowdown=4.0))
-        awf = kernel_ms(spin.make_schedule("AWF", num_workers=P, slow_workers=P // 2, slowdown=4.0))
+        P = spin.si_default_workers(W, spin.make_schedule("FAC", group=8))
+        static = kernel_ms(spin.make_schedule("STATIC", num_workers=P, group=8, slow_workers=P // 2, slowdown=4.0))
+        fac = kernel_ms(spin.make_schedule("FAC", num_workers=P, group=8, slow_workers=P // 2, slowdown=4.0))
+        awf = kernel_ms(spin.make_schedule("AWF", num_workers=P, group=8, slow_workers=P // 2, slowdown=4.0))
         assert awf <= 0.7 * static, (awf, static)
         assert awf <= 1.3 * fac, (awf, fac)
     finally:
