@@ -199,11 +199,11 @@ __device__ __forceinline__ void eval_pair(const PairDist &pd, const float4 NX, c
     // is never -0 (halfW - beta/B rounds an exact zero to +0)
     const bool in = live & (ca >= k.cosS) & (__float_as_uint(u) < __float_as_uint(k.umax)) & (a2 < k.amax2);
     if (PROBE && in) atomicAdd(pc_s, 1);
-    // alpha through the approximate reciprocal square root; the support
-    // decision above does not depend on it, and 16-bit quantisation absorbs
-    // its last-bit error
-    float r;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(fmaxf(a2, 1e-30f)));  // argument is normal
+    // alpha through the approximate square root (zero for a2 = 0); the
+    // support decision above does not depend on it, and 16-bit quantisation
+    // absorbs its last-bit error
+    float alpha;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(alpha) : "f"(a2));
     // U = rn(u * 2^16): u * 2^16 is exact and below 2^23 (0 <= u < W - 1 <= 127
     // for a contributing pair), so adding 2^23 rounds it to an integer held in
     // the low 23 bits; the low 16 bits are the fraction, the top 16 the row
@@ -211,7 +211,7 @@ __device__ __forceinline__ void eval_pair(const PairDist &pd, const float4 NX, c
     // W - 1 with a zero fraction: the column test bounds alpha, not the
     // approximate v, which may exceed W - 1 by a few ulps
     const uint32_t Ub = __float_as_uint(fmaf(u, 65536.0f, 8388608.0f));
-    const uint32_t Vb = min(__float_as_uint(fmaf(a2 * r, k.invB * 65536.0f, 8388608.0f)),
+    const uint32_t Vb = min(__float_as_uint(fmaf(alpha, k.invB * 65536.0f, 8388608.0f)),
                             0x4B000000u + ((uint32_t)k.umax << 16));
     const uint32_t A = Ub & 0xFFFFu, Bq = Vb & 0xFFFFu;
     const uint32_t w11 = (A * Bq + 32768u) >> 16;
