@@ -1041,8 +1041,12 @@ void launch_spin_kernel(const LaunchArgs &a, int blocks, size_t smem, cudaStream
         spin_kernel<false, kModeAll><<<blocks, kThreads, smem, stream>>>(a);
 }
 
+// Shared memory of a block that leaves room for two blocks per SM (228 KB per
+// SM, of which the system reserves 1 KB per block).
+constexpr size_t kTwoBlockSmem = (size_t)113 * 1024;
+
 // Largest group (power of two, <= 32, or the requested one) whose images fit
-// next to the fixed shared-memory layout with two blocks per SM.
+// next to the fixed shared-memory layout within the build's per-block budget.
 int choose_log2_group(int W, int requested_group) {
     if (requested_group > 0) {
         int l = 0;
@@ -1058,7 +1062,7 @@ int choose_log2_group(int W, int requested_group) {
         }
     // wide images: when the budget leaves at most two images per group, four
     // images at two blocks per SM feed each tile better
-    if (l <= 1 && spin_smem_bytes(W, l + 1) <= (size_t)113 * 1024) ++l;
+    if (l <= 1 && spin_smem_bytes(W, l + 1) <= kTwoBlockSmem) ++l;
     return l;
 }
 
