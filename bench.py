@@ -470,18 +470,19 @@ def bench_single(spin, torch, dev, c, steps, warmup, flush, stream, kinds=("STAT
         mesh = spin.si_mesh_create(tp, tn, n, stream)
         culled = torch.zeros(m, dtype=torch.int64, device=dev)
         support = torch.zeros(m, dtype=torch.int64, device=dev)
+        examined = torch.zeros(m, dtype=torch.int64, device=dev)
         spin.si_generate_probe(mesh, tq, m, W, B, cs, spin.make_schedule("GSS"), out, culled=culled,
-                               support=support, stream=stream)
+                               support=support, examined=examined, stream=stream)
         torch.cuda.synchronize()
         spin.si_get_stats(mesh)
         spin.si_mesh_destroy(mesh)
-        nc, ns = int(culled.sum().item()), int(support.sum().item())
+        nc, ns, ne = int(culled.sum().item()), int(support.sum().item()), int(examined.sum().item())
         best = min(res, key=lambda k: res[k]["kernel_ms"])
         peaks, _ = _measured_peaks()
         alu_peak = sms_count(torch, dev) * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
         ops = OPS_PER_CULLED * nc + OPS_PER_SUPPORT * ns
-        line.update(culled_pairs_per_step=nc, support_pairs_per_step=ns,
-                    culled_pairs_per_s=nc / (res[best]["ms_per_step"] / 1e3),
+        line.update(culled_pairs_per_step=nc, support_pairs_per_step=ns, examined_pairs_per_step=ne,
+                    stencil_overhead=ne / max(1, nc), culled_pairs_per_s=nc / (res[best]["ms_per_step"] / 1e3),
                     alu_frac=ops / (res[best]["kernel_ms"] / 1e3) / alu_peak, alu_frac_rule=best)
     del out
     return line
@@ -787,7 +788,11 @@ def _small_workload(name):
     if name == "sphere":
         return wl.plain_sphere()
     if name == "scene":
-        return wl.large_scene()
+        # the 1M-point scene with an eighth of its queries: 537 MB of images,
+        # above L2 and small enough for a many-pass profiler capture
+        c = wl.large_scene(m=32768)
+        c["name"] = "scene-1M-W64, 32,768 of its queries"
+        return c
     raise ValueError(name)
 
 

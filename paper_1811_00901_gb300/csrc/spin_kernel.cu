@@ -99,12 +99,19 @@ constexpr int shape_smem(int W, int log2S, int tn) {
     return off_tiles() + kStages * 32 * tn + 4 * img_words_of(W, log2S);
 }
 
-// Candidates per tile for a group shape.  Producer-ring shapes (<= 4 images)
-// take kTileMax.  Block-barrier shapes take the largest tile, a whole number
-// of unrolled trips (2 x kWarps x 32/S candidates), that keeps SI_MIN_BLOCKS
-// blocks per SM, else kTileMax.
+// Candidates per tile for a group shape.  Block-barrier shapes take the
+// largest tile, a whole number of unrolled trips (2 x kWarps x 32/S
+// candidates), that keeps SI_MIN_BLOCKS blocks per SM, else kTileMax.
+// Producer-ring shapes (<= 4 images) take the largest tile in [kTileMin,
+// kTileMax] that deals the same number of trips to every consumer warp, else
+// kTileMax: a warp with a trip more than the others holds its stage back.
 constexpr int tile_for_shape(int W, int log2S) {
-    if (log2S <= 2) return kTileMax;
+    if (log2S <= 2) {
+        const int unit = 2 * kProdConsumers * (32 >> log2S);
+        for (int tn = kTileMax; tn >= kTileMin; tn -= 16)
+            if (tn % unit == 0) return tn;
+        return kTileMax;
+    }
     const int unit = 2 * kWarps * (32 >> log2S);
     for (int tn = kTileMax; tn >= kTileMin; tn -= 16)
         if (tn % unit == 0 && shape_smem(W, log2S, tn) <= SI_SMEM_BUDGET_KB * 1024) return tn;
