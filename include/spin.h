@@ -105,7 +105,8 @@ typedef enum si_binning {
 typedef struct si_schedule {
     int32_t kind;        /* si_sched_kind */
     int32_t min_chunk;   /* lower bound of a dynamic chunk, in groups (0 -> 1) */
-    int32_t num_workers; /* persistent thread blocks P (0 -> all SMs x blocks per SM) */
+    int32_t num_workers; /* persistent thread blocks P (0 -> all SMs x blocks per SM, the count
+                            si_default_workers returns) */
     int32_t group;       /* images per group: 1, 2, 4, 8, 16 or 32 (0 -> by W) */
     int32_t grid_div;    /* grid cells per candidate radius, 1..16 (0 -> 8) */
     int32_t slices;      /* blocks that share one group's candidate stream, 1..64; each adds
