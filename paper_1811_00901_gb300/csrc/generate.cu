@@ -90,7 +90,7 @@ si_status check_item(const si_batch_item &it, const si_schedule &sc, int dev) {
         return SI_ERR_INVALID;
     }
     const int l2 = choose_log2_group(it.W, sc.group);
-    if (spin_smem_bytes(it.W, l2) > (size_t)227 * 1024) {
+    if (spin_smem_bytes(it.W, l2) > kMaxBlockSmem) {
         set_error("W = %d with group %d needs more shared memory than a block has", it.W, 1 << l2);
         return SI_ERR_INVALID;
     }
@@ -147,7 +147,7 @@ si_status si_default_workers(int32_t W, const si_schedule *schedule, int32_t *wo
     }
     const int l2 = choose_log2_group(W, group);
     const size_t smem = spin_smem_bytes(W, l2);
-    if (smem > (size_t)227 * 1024) {
+    if (smem > kMaxBlockSmem) {
         set_error("W = %d with group %d needs more shared memory than a block has", W, 1 << l2);
         return SI_ERR_INVALID;
     }

@@ -54,6 +54,7 @@ constexpr int kTileMin = SI_TILE_MIN;
 constexpr int kStages = SI_STAGES;  // tile ring depth
 constexpr int kMaxRows = 512;       // stencil rows held in shared memory at once
 constexpr int kMaxW = 128;
+constexpr size_t kMaxBlockSmem = (size_t)227 * 1024;  // dynamic shared memory one block may opt into
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // bounded device waits: 2 s
 constexpr uint64_t kSlowIdleCapNs = 1000000000ull;  // heterogeneity emulation: idle at most 1 s per step
 
