@@ -673,8 +673,10 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
     // A thread moves up to four images of one pixel with one shared read; the
     // threads of a warp take consecutive quads of a pixel, then consecutive
     // pixels, so the shared reads stay conflict-free and each warp store
-    // writes whole 32-byte sectors of 32 / (S/4) pixels per image (a partial
-    // sector costs a transfer of its own when the output is host memory).
+    // writes min(32, 128 / S) consecutive pixels of each image it touches:
+    // whole 32-byte sectors for groups of up to 16 images, half sectors for
+    // 32 (a partial sector costs a transfer of its own when the output is host
+    // memory).
     long long pix = 0;
     const int npix = W * W;
     int32_t *__restrict__ out = it.out;
