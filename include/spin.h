@@ -246,8 +246,9 @@ si_status si_generate_host(const float *points, const float *normals, int64_t n,
  *   needing more steps is SI_ERR_INVALID (raise min_chunk or group).
  *   The mesh's grid for this W, bin size and grid_div must exist already
  *   (si_mesh_prepare); otherwise SI_ERR_INVALID.
- *   Schedules: STATIC, SS, GSS or FAC with bilinear binning and no slow
- *   workers; anything else is SI_ERR_INVALID.
+ *   Schedules: STATIC, SS, GSS or FAC with bilinear binning, no slow
+ *   workers and one slice per group (slices 0 or 1); anything else is
+ *   SI_ERR_INVALID.
  *   The first call on a device (with it current) looks up the array's device
  *   address; make that first call before any stream capture.
  *   Calls share the array: two calls whose work overlaps on the GPU race. */
@@ -345,6 +346,25 @@ int64_t si_kernel_launches(void);
  * (Algorithm 1's tempSpinImage[k, l]++), which no vendor figure covers.
  * Synchronises `stream`. */
 si_status si_peak_smem_atomics(int32_t mode, double *atomics_per_s, si_stream stream);
+
+/* si_alloc_stats -- the library's device-memory accounting (the paper has no
+ * counterpart; it lets a caller, or a test, see whether a call allocated).
+ *   calls         : device allocations the library has made in this process
+ *                   (all devices); every one goes through the current
+ *                   device's default memory pool (cudaMallocAsync).
+ *   pool_used     : bytes of the current device's default pool in use now,
+ *   pool_reserved : bytes that pool holds from the device now (both count
+ *                   every user of the default pool, not only this library).
+ * Each pointer may be NULL.  SI_ERR_CUDA if the pool cannot be queried. */
+si_status si_alloc_stats(int64_t *calls, int64_t *pool_used, int64_t *pool_reserved);
+
+/* si_debug_fail_allocs -- host-side failure injection (the paper has no
+ * counterpart): after `skip` more device allocations succeed, the library's
+ * next `count` device allocations fail as if the device were out of memory,
+ * so the calls that make them return SI_ERR_OOM, free what they had taken and
+ * enqueue nothing more.  count = 0 disarms it.  Process-wide (all threads and
+ * devices); no GPU fault is involved.  SI_ERR_INVALID for negative values. */
+si_status si_debug_fail_allocs(int64_t skip, int64_t count);
 
 /* ------------------------------------------------------------- matching --
  * si_match -- spin-image matching: for each scene image its k best model

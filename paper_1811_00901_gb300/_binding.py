@@ -102,6 +102,9 @@ _SIGNATURES = {
     "si_version": ([], ctypes.c_char_p),
     "si_kernel_launches": ([], ctypes.c_int64),
     "si_peak_smem_atomics": ([ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
+    "si_alloc_stats": ([ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                        ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "si_debug_fail_allocs": ([ctypes.c_int64, ctypes.c_int64], ctypes.c_int),
 }
 
 _lib = None
@@ -389,6 +392,17 @@ def si_version():
 
 def si_kernel_launches():
     return int(load().si_kernel_launches())
+
+
+def si_alloc_stats():
+    """(allocation calls so far, pool bytes in use, pool bytes reserved) of the current device."""
+    c, u, r = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().si_alloc_stats(ctypes.byref(c), ctypes.byref(u), ctypes.byref(r)))
+    return c.value, u.value, r.value
+
+
+def si_debug_fail_allocs(skip, count):
+    _check(load().si_debug_fail_allocs(int(skip), int(count)))
 
 
 def si_peak_smem_atomics(mode=0, stream=None):

@@ -542,7 +542,7 @@ struct GraphEntry {
     std::vector<char> key;
     std::vector<const Mesh *> meshes;
     cudaGraphExec_t exec = nullptr;
-    char *scratch = nullptr;  // persistent for the entry's lifetime
+    char *scratch = nullptr;  // pool memory, persistent for the entry's lifetime
     cudaEvent_t last = nullptr;
     int kernels = 0;
     int device = 0;
@@ -560,7 +560,10 @@ void destroy_entry(GraphEntry &e) {
         cudaEventDestroy(e.last);
     }
     if (e.exec) cudaGraphExecDestroy(e.exec);
-    if (e.scratch) cudaFree(e.scratch);
+    if (e.scratch) {
+        dev_free(e.scratch, nullptr);
+        cudaStreamSynchronize(nullptr);
+    }
     cudaSetDevice(prev);
 }
 
@@ -640,8 +643,11 @@ si_status enqueue_batch_graph(const std::vector<si_batch_item> &items, const std
     e.key = key;
     e.device = dev;
     for (const auto &it : items) e.meshes.push_back(reinterpret_cast<const Mesh *>(it.mesh));
-    cudaError_t err = cudaMalloc(&e.scratch, p.total_bytes);
-    if (err != cudaSuccess) return cuda_fail(err, "cudaMalloc(batch graph scratch)");
+    // the entry's scratch lives as long as the entry: taken from the pool in
+    // stream order before capture, returned when the entry is destroyed
+    st = dev_alloc((void **)&e.scratch, p.total_bytes, stream);
+    if (st != SI_OK) return st;
+    cudaError_t err = cudaSuccess;
     std::vector<char> blob;
     fill_blob(p, items, {}, e.scratch, &blob);
     // the descriptor blob is uploaded once, outside the graph, in stream order

@@ -1,5 +1,6 @@
 // common.cu -- error reporting, stream-ordered allocation, the pinned staging
 // ring for host->device uploads, and device queries.
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -41,12 +42,38 @@ static void ensure_pool(int dev) {
     g_pool_ready[dev] = true;
 }
 
+// Accounting and host-side failure injection: every device allocation of the
+// library goes through dev_alloc, which counts it and, while an injection is
+// armed, lets `g_inject_skip` more allocations through and then fails the next
+// `g_inject_fail` as if the device were out of memory.
+static std::atomic<int64_t> g_alloc_calls{0};
+static std::mutex g_inject_mu;
+static int64_t g_inject_skip = 0, g_inject_fail = 0;
+static std::atomic<bool> g_inject_armed{false};
+
+static bool injected_failure() {
+    if (!g_inject_armed.load()) return false;
+    std::lock_guard<std::mutex> lk(g_inject_mu);
+    if (g_inject_fail <= 0) return false;
+    if (g_inject_skip > 0) {
+        --g_inject_skip;
+        return false;
+    }
+    if (--g_inject_fail == 0) g_inject_armed.store(false);
+    return true;
+}
+
 si_status dev_alloc(void **p, size_t bytes, cudaStream_t stream) {
     int dev = 0;
     SI_CUDA(cudaGetDevice(&dev));
     ensure_pool(dev);
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    g_alloc_calls.fetch_add(1);
+    if (injected_failure()) {
+        set_error("device allocation of %zu bytes failed: injected failure (si_debug_fail_allocs)", bytes);
+        return SI_ERR_OOM;
+    }
     cudaError_t e = cudaMallocAsync(p, bytes, stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -168,3 +195,35 @@ void si_set_timing(int32_t enabled) { si::g_timing.store(enabled ? 1 : 0); }
 int64_t si_kernel_launches(void) { return (int64_t)si::g_launches.load(); }
 
 }  // extern "C"
+
+extern "C" si_status si_alloc_stats(int64_t *calls, int64_t *pool_used, int64_t *pool_reserved) {
+    if (calls) *calls = si::g_alloc_calls.load();
+    if (pool_used || pool_reserved) {
+        int dev = 0;
+        SI_CUDA(cudaGetDevice(&dev));
+        cudaMemPool_t pool;
+        SI_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+        uint64_t v = 0;
+        if (pool_used) {
+            SI_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v));
+            *pool_used = (int64_t)v;
+        }
+        if (pool_reserved) {
+            SI_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &v));
+            *pool_reserved = (int64_t)v;
+        }
+    }
+    return SI_OK;
+}
+
+extern "C" si_status si_debug_fail_allocs(int64_t skip, int64_t count) {
+    if (skip < 0 || count < 0) {
+        si::set_error("si_debug_fail_allocs: skip and count must be >= 0");
+        return SI_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(si::g_inject_mu);
+    si::g_inject_skip = skip;
+    si::g_inject_fail = count;
+    si::g_inject_armed.store(count > 0);
+    return SI_OK;
+}

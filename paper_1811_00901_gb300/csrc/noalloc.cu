@@ -28,6 +28,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "chunk_rule.h"
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -51,30 +52,14 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 std::mutex g_addr_mu;
 void *g_addr[64] = {nullptr};
 
-// One scheduling step's chunk (same rules as the library's chunk tables).
-__host__ __device__ inline int64_t next_chunk(int kind, int64_t step, int64_t rem, int64_t P, int64_t mc,
-                                              int64_t *fac_c) {
-    int64_t c;
-    if (kind == SI_SCHED_SS) {
-        c = mc;
-    } else if (kind == SI_SCHED_GSS) {
-        c = (rem + P - 1) / P;
-        if (c < mc) c = mc;
-    } else {  // FAC
-        if (step % P == 0) {
-            *fac_c = (rem + 2 * P - 1) / (2 * P);
-            if (*fac_c < mc) *fac_c = mc;
-        }
-        c = *fac_c;
-    }
-    return c < rem ? c : rem;
-}
-
-int64_t count_steps(int kind, int64_t units, int64_t P, int64_t mc) {
+// Scheduling steps of a call under `kind`, counted with the library's one
+// chunk rule (chunk_rule_next); the count stops at `limit` + 1, so a call
+// with far more steps than the scratch holds is refused without walking them.
+int64_t count_steps(int kind, int64_t units, int64_t P, int64_t mc, int64_t limit) {
     if (kind == SI_SCHED_STATIC) return P;
     int64_t done = 0, step = 0, fac_c = 0;
-    while (done < units) {
-        done += next_chunk(kind, step, units - done, P, mc, &fac_c);
+    while (done < units && step <= limit) {
+        done += chunk_rule_next(kind, step, units - done, P, mc, &fac_c);
         ++step;
     }
     return step;
@@ -105,9 +90,11 @@ __global__ void noalloc_setup_kernel(ItemDesc desc, int kind, int units, int P, 
             pieces[s] = Piece{0, (int)lo, (int)hi, 0};
         }
     } else if (tid == 0) {
+        // GSS and FAC: each chunk depends on what the earlier ones left, so one
+        // thread walks the steps with the library's chunk rule
         int64_t done = 0, fac_c = 0;
         for (int s = 0; s < nsteps; ++s) {
-            const int64_t c = next_chunk(kind, s, units - done, P, mc, &fac_c);
+            const int64_t c = chunk_rule_next(kind, s, units - done, P, mc, &fac_c);
             pieces[s] = Piece{0, (int)done, (int)(done + c), 0};
             done += c;
         }
@@ -145,8 +132,10 @@ extern "C" si_status si_generate_noalloc(si_mesh_t mesh, const int32_t *query_id
     const si_batch_item it{mesh, query_idx, m, W, bin_size, cos_support_angle, out};
     si_status s = check_item(it, schedule, dev);
     if (s != SI_OK) return s;
-    if (schedule.kind >= SI_SCHED_FAC_PROB || schedule.binning != SI_BIN_BILINEAR || schedule.slow_workers != 0) {
-        set_error("si_generate_noalloc: takes STATIC, SS, GSS or FAC, bilinear binning and no slow workers");
+    if (schedule.kind >= SI_SCHED_FAC_PROB || schedule.binning != SI_BIN_BILINEAR || schedule.slow_workers != 0 ||
+        schedule.slices > 1) {
+        set_error("si_generate_noalloc: takes STATIC, SS, GSS or FAC, bilinear binning, no slow workers and one "
+                  "slice per group");
         return SI_ERR_INVALID;
     }
     if (m == 0) return SI_OK;
@@ -176,11 +165,11 @@ extern "C" si_status si_generate_noalloc(si_mesh_t mesh, const int32_t *query_id
     }
     const int P = schedule.num_workers > 0 ? schedule.num_workers : num_sms(dev) * per_sm;
     const int mc = schedule.min_chunk > 0 ? schedule.min_chunk : 1;
-    const int64_t nsteps = count_steps(schedule.kind, units, P, mc);
+    const int64_t nsteps = count_steps(schedule.kind, units, P, mc, kNoAllocMaxSteps);
     if (nsteps > kNoAllocMaxSteps) {
-        set_error("si_generate_noalloc: %lld scheduling steps exceed the %d that fit in its %zu-byte scratch; "
+        set_error("si_generate_noalloc: more than the %d scheduling steps that fit in its %zu-byte scratch; "
                   "use a larger min_chunk, group or fewer workers",
-                  (long long)nsteps, kNoAllocMaxSteps, kNoAllocScratchBytes);
+                  kNoAllocMaxSteps, kNoAllocScratchBytes);
         return SI_ERR_INVALID;
     }
     unsigned char *scratch = nullptr;

@@ -4,9 +4,9 @@
 // kernel's workers claim, one atomic increment of the step index per request.
 //
 // Readings: the scheduling step advances by one per assignment and every chunk
-// is clamped to the iterations that remain; GSS never goes below min_chunk;
-// FAC hands out batches of P equal chunks of ceil(R / (2P)) (FAC2), R being
-// what remains when the batch starts; FAC_PROB takes the batch chunk from the
+// is clamped to the iterations that remain; SS, GSS and FAC (FAC2) take their
+// chunks from chunk_rule_next (chunk_rule.h, shared with the device code of the
+// allocation-free entry point); FAC_PROB takes the batch chunk from the
 // original factoring rule (Hummel, Schonberg and Flynn 1992) for iterations
 // whose times have coefficient of variation cov; STATIC gives worker k the
 // block [floor(kN/P), floor((k+1)N/P)).
@@ -14,6 +14,7 @@
 #include <cmath>
 #include <vector>
 
+#include "chunk_rule.h"
 #include "internal.h"
 
 namespace si {
@@ -41,23 +42,14 @@ int64_t chunk_table(int kind, int64_t units, int workers, int min_chunk, double 
     while (done < units) {
         const int64_t rem = units - done;
         int64_t c;
-        switch (kind) {
-            case SI_SCHED_SS:
-                c = mc;
-                break;
-            case SI_SCHED_GSS:
-                c = std::max(mc, (rem + P - 1) / P);
-                break;
-            case SI_SCHED_FAC_PROB:
-                if (step % P == 0) fac_c = std::max(mc, fac_prob_chunk(step / P, rem, P, cov));
-                c = fac_c;
-                break;
-            default:  // SI_SCHED_FAC
-                if (step % P == 0) fac_c = std::max(mc, (rem + 2 * P - 1) / (2 * P));
-                c = fac_c;
-                break;
+        if (kind == SI_SCHED_FAC_PROB) {
+            if (step % P == 0) fac_c = std::max(mc, fac_prob_chunk(step / P, rem, P, cov));
+            c = std::min(fac_c, rem);
+        } else {
+            // SS, GSS, FAC (and any other kind as FAC): the rule every caller shares
+            c = chunk_rule_next(kind == SI_SCHED_SS || kind == SI_SCHED_GSS ? kind : SI_SCHED_FAC, step, rem, P, mc,
+                                &fac_c);
         }
-        c = std::min(c, rem);
         done += c;
         starts->push_back(done);
         ++step;

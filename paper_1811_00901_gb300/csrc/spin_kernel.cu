@@ -25,11 +25,15 @@
 //     behind a branch.  Full tiles take a loop without per-lane range checks.
 //
 // Per pair (P = query, X = candidate, FP32, differences taken directly):
-//   d = X - P; cull if fl32(|d|^2) > Rc2; angle test n.n_X >= cos S;
-//   beta = n.d; alpha^2 = |d|^2 - beta^2 (Algorithm 1's form, clamped at 0);
+//   d = X - P; angle test n.n_X >= cos S; beta = n.d;
+//   alpha^2 = |d - beta n|^2 (the part of d orthogonal to n: Algorithm 1's
+//   |d|^2 - beta^2 for a unit n, without its cancellation near the normal
+//   axis, where FP32 |d|^2 - beta^2 loses alpha to sqrt(eps) |d|);
 //   u = W/2 - beta/B; support test 0 <= u < W-1 and alpha^2 < ((W-1)B)^2
 //   (i.e. v = alpha/B < W-1); v = alpha/B; fixed-point bilinear splat of
-//   weight 65536 with four shared-memory int32 atomics.
+//   weight 65536 with four shared-memory int32 atomics.  The candidate cull
+//   fl32(|d|^2) <= Rc2 is implied by the support test (every contributing
+//   pair has |d|^2 < R^2 < Rc2), so only probes evaluate it.
 // Images hold (W+1) x (W+1) words per slot: the extra row and column absorb
 // the zero-weight corners of points whose coordinate rounds up onto W-1.
 #include <atomic>
@@ -168,18 +172,19 @@ struct Shape {
     __device__ __forceinline__ int row_words() const { return (W() + 1) << log2S(); }
 };
 
-// The distance part of a pair: d = X - P and the candidate-set expression,
-// exactly fl32(fma(dz,dz, fma(dy,dy, dx*dx))).
+// The distance part of a pair: d = X - P and, when D2, the candidate-set
+// expression, exactly fl32(fma(dz,dz, fma(dy,dy, dx*dx))).
 struct PairDist {
     float dx, dy, dz, d2;
 };
 
+template <bool D2>
 __device__ __forceinline__ PairDist pair_dist(const float4 X, const float4 P) {
     PairDist r;
     r.dx = __fsub_rn(X.x, P.x);
     r.dy = __fsub_rn(X.y, P.y);
     r.dz = __fsub_rn(X.z, P.z);
-    r.d2 = __fmaf_rn(r.dz, r.dz, __fmaf_rn(r.dy, r.dy, __fmul_rn(r.dx, r.dx)));
+    r.d2 = D2 ? __fmaf_rn(r.dz, r.dz, __fmaf_rn(r.dy, r.dy, __fmul_rn(r.dx, r.dx))) : 0.0f;
     return r;
 }
 
@@ -189,26 +194,30 @@ constexpr int kMagicHi = 0x4B00;
 
 // Evaluates the rest of one (query, candidate) pair and splats it when it
 // contributes.  Every contributing pair has |d|^2 < R^2 < Rc2, so the cull
-// itself is not part of the support decision.  `img_adj` is the slot's pixel
-// (0, 0) moved back by the exponent bias that the raw coordinate bits carry
-// (kMagicHi rows and kMagicHi columns).
+// is not part of the support decision (`live` is the lane's range check).
+// `img_adj` is the slot's pixel (0, 0) moved back by the exponent bias that
+// the raw coordinate bits carry (kMagicHi rows and kMagicHi columns).
 template <int WT, int LS, bool PROBE>
 __device__ __forceinline__ void eval_pair(const PairDist &pd, const float4 NX, const bool live, const float4 N,
                                           const PairConsts &k, const Shape<WT, LS> sh, int *img_adj, int &cnt,
                                           int *pc_s) {
-    const float dx = pd.dx, dy = pd.dy, dz = pd.dz, d2 = pd.d2;
+    const float dx = pd.dx, dy = pd.dy, dz = pd.dz;
     const float ca = fmaf(N.z, NX.z, fmaf(N.y, NX.y, N.x * NX.x));
     const float beta = fmaf(N.z, dz, fmaf(N.y, dy, N.x * dx));
-    const float a2 = fmaxf(fmaf(-beta, beta, d2), 0.0f);
+    // alpha^2 from r = d - beta n: an error in beta moves r along n, which
+    // changes |r|^2 only to second order, so alpha keeps ~1e-7 relative
+    // accuracy even on the normal axis
+    const float rx = fmaf(-beta, N.x, dx), ry = fmaf(-beta, N.y, dy), rz = fmaf(-beta, N.z, dz);
+    const float a2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
     const float u = fmaf(-beta, k.invB, k.halfW);
     // 0 <= u < W-1 as one unsigned compare of the float bits: non-negative floats
     // order like their bits, negatives (sign bit) and NaN compare above umax; u
     // is never -0 (halfW - beta/B rounds an exact zero to +0)
     const bool in = live & (ca >= k.cosS) & (__float_as_uint(u) < __float_as_uint(k.umax)) & (a2 < k.amax2);
     if (PROBE && in) atomicAdd(pc_s, 1);
-    // alpha through the approximate square root (zero for a2 = 0); the
-    // support decision above does not depend on it, and 16-bit quantisation
-    // absorbs its last-bit error
+    // alpha through the approximate square root (zero for a2 = 0, and a2 is a
+    // sum of squares, never negative); the support decision above does not
+    // depend on it, and 16-bit quantisation absorbs its last-bit error
     float alpha;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(alpha) : "f"(a2));
     // U = rn(u * 2^16): u * 2^16 is exact and below 2^23 (0 <= u < W - 1 <= 127
@@ -266,7 +275,9 @@ __device__ __forceinline__ void trip(const float4 *p0, const float4 *p1, const b
                                      const float4 P, const float4 N, const PairConsts &k, const Shape<WT, LS> sh,
                                      int *img_adj, int &cnt, int *pc_c, int *pc_s, unsigned *pc_h) {
     const float4 X0 = p0[0], X1 = p1[0];
-    const PairDist d0 = pair_dist(X0, P), d1 = pair_dist(X1, P);
+    // |d|^2: the nearest-bin count's spelled-out alpha and the probes' cull need it
+    constexpr bool kD2 = PROBE || NB;
+    const PairDist d0 = pair_dist<kD2>(X0, P), d1 = pair_dist<kD2>(X1, P);
     const bool near0 = l0 & (d0.d2 <= k.Rc2), near1 = l1 & (d1.d2 <= k.Rc2);
     if (PROBE) {
         if (near0) {
@@ -284,8 +295,8 @@ __device__ __forceinline__ void trip(const float4 *p0, const float4 *p1, const b
         eval_pair_nearest<WT, LS, PROBE>(d0, N0, near0, N, k, sh, img_adj, cnt, pc_s);
         eval_pair_nearest<WT, LS, PROBE>(d1, N1, near1, N, k, sh, img_adj, cnt, pc_s);
     } else {
-        eval_pair<WT, LS, PROBE>(d0, N0, near0, N, k, sh, img_adj, cnt, pc_s);
-        eval_pair<WT, LS, PROBE>(d1, N1, near1, N, k, sh, img_adj, cnt, pc_s);
+        eval_pair<WT, LS, PROBE>(d0, N0, l0, N, k, sh, img_adj, cnt, pc_s);
+        eval_pair<WT, LS, PROBE>(d1, N1, l1, N, k, sh, img_adj, cnt, pc_s);
     }
 }
 

@@ -206,6 +206,48 @@ def object_scene(n, seed, n_objects=64, density_range=(1.0, 50.0)):
     return _f32(np.concatenate(pts)), _f32(np.concatenate(nrms))
 
 
+def needle_layers(half_height, seed, axis=(0.31, -0.22, 0.93), origin=(0.4, 0.55, 0.3)):
+    """Points along and across one tilted axis, all with the axis as normal:
+    a needle of points on the axis (half of them exactly on it, half within
+    0.02 h of it) at heights t = h (-0.9 + 0.00231 k), and five parallel discs
+    (radius 0.3 h) perpendicular to the axis at heights h x {-0.75, -0.34, 0,
+    0.28, 0.625}.  Pairs between them lie close to each other's normal axis at
+    distances up to ~2h, the case where alpha, the distance from the axis, is
+    small next to |X - P|.  No height difference comes within 5e-4 bins of a
+    row threshold (u = 0 or u = W - 1) of a W x W image with half-height h
+    for W in {16, 32, 64, 128}, and every alpha stays far below the last
+    column, so no pair is near a support threshold.
+
+    Returns (points, normals, t, lateral): t[k] the height along the axis and
+    lateral[k] the in-plane offset (2 components) of point k before rounding
+    to FP32."""
+    rng = _rng(seed)
+    h = float(half_height)
+    n = np.asarray(axis, np.float64)
+    n /= np.linalg.norm(n)
+    e1 = np.cross(n, [1.0, 0.0, 0.0])
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(n, e1)
+    t_needle = h * (-0.9 + 0.00231 * np.arange(int(1.85 / 0.00231) + 1))
+    k = t_needle.size
+    lat_needle = np.zeros((k, 2))
+    r = rng.uniform(0.0, 0.02 * h, k // 2)
+    a = rng.uniform(0.0, 2.0 * math.pi, k // 2)
+    lat_needle[1::2][: k // 2] = np.stack([r * np.cos(a), r * np.sin(a)], 1)[: lat_needle[1::2].shape[0]]
+    ts, lats = [t_needle], [lat_needle]
+    for f in (-0.75, -0.34, 0.0, 0.28, 0.625):
+        m = 400
+        rr = 0.3 * h * np.sqrt(rng.uniform(0.0, 1.0, m))
+        aa = rng.uniform(0.0, 2.0 * math.pi, m)
+        ts.append(np.full(m, f * h))
+        lats.append(np.stack([rr * np.cos(aa), rr * np.sin(aa)], 1))
+    t = np.concatenate(ts)
+    lat = np.concatenate(lats)
+    pts = np.asarray(origin, np.float64) + t[:, None] * n + lat[:, :1] * e1 + lat[:, 1:] * e2
+    nrm = np.tile(n, (t.size, 1))
+    return _f32(pts), _f32(nrm), t, lat
+
+
 def cos_deg(deg):
     """cos of a support angle in degrees, as the FP32 value passed to the library."""
     if deg >= 180.0:

@@ -47,16 +47,21 @@ def gpu_run(points, normals, W, B, cos_s, query_idx=None, m=None, schedule=None,
         spin.si_mesh_destroy(mesh)
 
 
-def compare_with_oracle(gpu_imgs, points, normals, W, B, cos_s, query_idx_all, sample, support=None):
+def compare_with_oracle(gpu_imgs, points, normals, W, B, cos_s, query_idx_all, sample, support=None,
+                        require_unflagged=False):
     """Compare GPU images (int32, [m, W, W]) at positions `sample` with the
     oracle.  Membership may differ only on boundary-flagged pairs: each flip
     moves at most weight 1, so the L1 allowance is 1e-4 * total + flagged.
-    Returns the worst L1 / total seen."""
+    With require_unflagged the sampled images must have no flagged pair at
+    all, so the bound is 1e-4 * total alone.  Returns the worst L1 / total
+    seen."""
     sample = np.asarray(sample)
     q = sample if query_idx_all is None else np.asarray(query_idx_all)[sample]
     img, sup, flg = oracle.spin_images(points, normals, W, B, cos_s, query_idx=q.astype(np.int32))
     worst = 0.0
     for k, s in enumerate(sample):
+        if require_unflagged:
+            assert flg[k] == 0, "image %d has %d flagged pairs" % (s, flg[k])
         g = gpu_imgs[s].astype(np.float64) / 65536.0
         tot = img[k].sum()
         l1 = np.abs(g - img[k]).sum()

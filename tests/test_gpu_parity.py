@@ -74,6 +74,22 @@ def test_object_scene_w64_query_list():
     np.testing.assert_array_equal(imgs[10], imgs[11])
 
 
+@pytest.mark.parametrize("W", [16, 32, 64])
+def test_near_axis_needle_and_layers(W):
+    """Points on and next to each query's normal axis at distances up to the
+    image half-height (a needle plus parallel discs, all sharing the axis as
+    normal, S = 180 deg), every image: alpha is small next to |X - P| there,
+    where |d|^2 - beta^2 in FP32 would lose alpha to cancellation.  No pair is
+    near a threshold, so the bound holds with no flagged allowance."""
+    h = 0.16
+    B = float(np.float32(2 * h / W))
+    pts, nrm, _, _ = wl.needle_layers(h, 1)
+    imgs, pr = gpu_run(pts, nrm, W, B, -1.0, probe=True, schedule=None)
+    worst = compare_with_oracle(imgs, pts, nrm, W, B, -1.0, None, np.arange(pts.shape[0]), support=pr["support"],
+                                require_unflagged=True)
+    assert worst <= 1e-4
+
+
 @pytest.mark.parametrize("W,B,deg", [(2, 0.1, 180.0), (5, 0.1, 180.0), (7, 0.07, 45.0), (127, 0.004, 60.0),
                                      (128, 0.004, 60.0)])
 def test_odd_widths(W, B, deg):

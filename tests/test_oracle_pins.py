@@ -219,18 +219,161 @@ def test_support_radius_bound():
         assert hs[k] != 0 or cnt[k] == 0
 
 
-def test_candidate_hash_is_order_independent():
-    pts, _ = wl.sphere(700, 2)
-    perm = np.random.default_rng(1).permutation(700)
+_FMIX_C1, _FMIX_C2 = 0x85EBCA6B, 0xC2B2AE35
+
+
+def _fmix32_np(h):
+    """MurmurHash3's 32-bit finaliser (Appleby), restated in NumPy from its
+    published definition: xor-shift 16, multiply, xor-shift 13, multiply,
+    xor-shift 16, all modulo 2^32."""
+    h = np.asarray(h, dtype=np.uint64) & 0xFFFFFFFF
+    h ^= h >> 16
+    h = (h * _FMIX_C1) & 0xFFFFFFFF
+    h ^= h >> 13
+    h = (h * _FMIX_C2) & 0xFFFFFFFF
+    h ^= h >> 16
+    return h
+
+
+def _unfmix32_np(h):
+    """Inverse of the finaliser: undo each xor-shift by repeated shifting and
+    each multiply by the modular inverse of its odd constant."""
+    def unxorshift(x, k):
+        y = x.copy()
+        for _ in range(32 // k + 1):
+            y = x ^ (y >> k)
+        return y
+    h = np.asarray(h, dtype=np.uint64) & 0xFFFFFFFF
+    h = unxorshift(h, 16)
+    h = (h * pow(_FMIX_C2, -1, 1 << 32)) & 0xFFFFFFFF
+    h = unxorshift(h, 13)
+    h = (h * pow(_FMIX_C1, -1, 1 << 32)) & 0xFFFFFFFF
+    h = unxorshift(h, 16)
+    return h
+
+
+def test_fmix32_restatement_is_the_published_bijection():
+    """The NumPy finaliser maps 0 to 0 and inverts exactly (every step of
+    fmix32 is a bijection of 32-bit words), so the restatement used below has
+    the published structure."""
+    x = np.random.default_rng(9).integers(0, 1 << 32, 100000, dtype=np.uint64)
+    assert int(_fmix32_np(0)) == 0
+    np.testing.assert_array_equal(_unfmix32_np(_fmix32_np(x)), x)
+    # the finaliser avalanches: one flipped input bit flips about half the output bits
+    flips = np.unpackbits((_fmix32_np(x) ^ _fmix32_np(x ^ 1)).astype(">u4").view(np.uint8)).mean() * 32
+    assert 14.0 < flips < 18.0
+
+
+def test_candidate_fingerprint_against_fp64_set():
+    """The candidate fingerprint is the sum, modulo 2^32, of fmix32 over the
+    ORIGINAL indices of the candidate set.  Pinned against an independent
+    computation: the FP64 distance set (on points whose FP64 distance is far
+    from the threshold, where FP32 rounding cannot decide membership) hashed
+    with the NumPy restatement.  A hash of another quantity (sorted position,
+    a position shifted by one, the query's own index) fails here."""
+    pts, _ = wl.sphere(1500, 12)
     W, B = 8, 0.1
-    cnt0, h0 = oracle.candidates_fp32(pts, W, B, query_idx=[0, 1, 2])
-    # move the three query points to the front so their indices stay 0, 1, 2
-    rest = [p for p in perm if p > 2]
-    order = np.array([0, 1, 2] + rest)
-    cnt1, h1 = oracle.candidates_fp32(pts[order], W, B, query_idx=[0, 1, 2])
-    np.testing.assert_array_equal(cnt0, cnt1)
-    # indices changed, so fingerprints generally differ; counts must not
-    assert h0.shape == h1.shape
+    rc2 = float(oracle.candidate_rc2(W, B))
+    P64 = pts.astype(np.float64)
+    q = np.arange(0, 1500, 29).astype(np.int32)
+    cnt, hs = oracle.candidates_fp32(pts, W, B, query_idx=q)
+    checked = 0
+    for k, qi in enumerate(q):
+        d2 = ((P64 - P64[qi]) ** 2).sum(1)
+        if np.any(np.abs(d2 - rc2) <= 1e-5 * rc2):
+            continue  # a point near the threshold: FP32 decides it, not this pin
+        members = np.nonzero(d2 <= rc2)[0]
+        assert cnt[k] == members.size
+        expect = int(_fmix32_np(members).sum() & 0xFFFFFFFF)
+        assert int(hs[k]) == expect
+        checked += 1
+    assert checked >= 40
+    # the same set under a permutation of the point order (indices follow the
+    # points) gives the same fingerprint
+    perm = np.random.default_rng(1).permutation(1500)
+    inv = np.argsort(perm)
+    cnt_p, hs_p = oracle.candidates_fp32(pts[perm], W, B, query_idx=inv[q].astype(np.int32))
+    np.testing.assert_array_equal(cnt_p, cnt)
+    relabel = [int(_fmix32_np(inv[np.nonzero(((P64 - P64[qi]) ** 2).sum(1) <= rc2)[0]]).sum() & 0xFFFFFFFF)
+               for qi in q]
+    far = [k for k, qi in enumerate(q) if not np.any(np.abs(((P64 - P64[qi]) ** 2).sum(1) - rc2) <= 1e-5 * rc2)]
+    assert all(int(hs_p[k]) == relabel[k] for k in far)
+
+
+@pytest.mark.parametrize("W", [16, 32, 64, 128])
+def test_near_axis_closed_form(W):
+    """Points on and next to the query's normal axis, where alpha is small
+    next to |X - P| (a needle and parallel discs, all with the axis as normal,
+    S = 180 deg).  By construction beta = t_X - t_P (heights along the axis)
+    and alpha = |lateral_X - lateral_P| (in-plane offsets), so the image is the
+    bilinear splat of those closed-form coordinates.  The oracle must match it
+    up to the FP32 rounding of the input points (about 1e-5 of the total), with
+    the support counts exact."""
+    h = 0.16
+    B = np.float32(2 * h / W)
+    pts, nrm, t, lat = wl.needle_layers(h, 1)
+    q = np.arange(0, pts.shape[0], 37).astype(np.int32)
+    img, sup, flg = oracle.spin_images(pts, nrm, W, float(B), -1.0, query_idx=q)
+    assert int(flg.sum()) == 0
+    Bd = float(B)
+    for k, qi in enumerate(q):
+        u = W / 2 - (t - t[qi]) / Bd
+        v = np.hypot(lat[:, 0] - lat[qi, 0], lat[:, 1] - lat[qi, 1]) / Bd
+        i, j = np.floor(u), np.floor(v)
+        ok = (i >= 0) & (i + 1 <= W - 1) & (j + 1 <= W - 1)
+        a, b = (u - i)[ok], (v - j)[ok]
+        ii, jj = i[ok].astype(int), j[ok].astype(int)
+        e = np.zeros((W, W))
+        np.add.at(e, (ii, jj), (1 - a) * (1 - b))
+        np.add.at(e, (ii + 1, jj), a * (1 - b))
+        np.add.at(e, (ii, jj + 1), (1 - a) * b)
+        np.add.at(e, (ii + 1, jj + 1), a * b)
+        assert int(ok.sum()) == int(sup[k])
+        assert np.abs(e - img[k]).sum() <= 5e-5 * e.sum()
+
+
+def _numpy_spin_images(pts, nrm, W, B, cos_s, q):
+    """An independent NumPy restatement for small inputs: alpha as the length
+    of n x d (equal to sqrt(|d|^2 - beta^2) for a unit n), the four corners
+    accumulated with np.add.at over all pairs at once."""
+    P = pts.astype(np.float64)
+    N = nrm.astype(np.float64)
+    N = N / np.linalg.norm(N, axis=1, keepdims=True)
+    out = np.zeros((len(q), W, W))
+    sup = np.zeros(len(q), np.int64)
+    for k, qi in enumerate(q):
+        d = P - P[qi]
+        beta = d @ N[qi]
+        alpha = np.linalg.norm(np.cross(N[qi], d), axis=1)
+        u = W / 2 - beta / B
+        v = alpha / B
+        i, j = np.floor(u), np.floor(v)
+        ok = (N @ N[qi] >= cos_s) & (i >= 0) & (i + 1 <= W - 1) & (j + 1 <= W - 1)
+        a, b = (u - i)[ok], (v - j)[ok]
+        ii, jj = i[ok].astype(int), j[ok].astype(int)
+        np.add.at(out[k], (ii, jj), (1 - a) * (1 - b))
+        np.add.at(out[k], (ii + 1, jj), a * (1 - b))
+        np.add.at(out[k], (ii, jj + 1), (1 - a) * b)
+        np.add.at(out[k], (ii + 1, jj + 1), a * b)
+        sup[k] = ok.sum()
+    return out, sup
+
+
+@pytest.mark.parametrize("seed,n,W,B,deg", [(1, 64, 6, 0.2, 60.0), (2, 50, 9, 0.11, 45.0), (3, 64, 4, 0.4, 180.0),
+                                            (4, 33, 16, 0.05, 90.0)])
+def test_numpy_cross_check_small(seed, n, W, B, deg):
+    """Brute force on tiny inputs: the oracle against an independent NumPy
+    restatement (cross-product alpha, vectorised splat) on n <= 64 points,
+    every image; pairs the oracle flags may differ by at most their weight."""
+    pts, nrm = wl.object_scene(n, seed, n_objects=3)
+    c = float(wl.cos_deg(deg))
+    q = np.arange(n).astype(np.int32)
+    img, sup, flg = oracle.spin_images(pts, nrm, W, np.float32(B), c, query_idx=q)
+    ref, rsup = _numpy_spin_images(pts, nrm, W, float(np.float32(B)), c, q)
+    assert sup.sum() > n  # the inputs exercise more than the self pairs
+    for k in range(n):
+        assert abs(int(sup[k]) - int(rsup[k])) <= flg[k]
+        assert np.abs(img[k] - ref[k]).sum() <= 1e-9 * max(1.0, ref[k].sum()) + flg[k]
 
 
 def test_query_subset_matches_full():
