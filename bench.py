@@ -195,14 +195,25 @@ def _ncu_traffic(workload):
 
 
 # Algorithmic ALU work, per unit (lane-operations; an FMA counts once):
-#   per culled pair (fl32 |X-P|^2 <= Rc2): difference (3), squared norm (3),
-#   compare (1), normal dot (3), compare (1)                        -> 11
-#   per contributing pair: beta (3), alpha^2 = |d|^2 - beta^2 (1), sqrt (1),
-#   u, v (2), support tests (3), fixed-point quantise and split (6),
-#   weights (5), address (2), four shared-memory int32 atomics (4), count (1)
-#                                                                    -> 28
-OPS_PER_CULLED = 11
-OPS_PER_SUPPORT = 28
+#   per culled pair (the candidate set, fl32 |X-P|^2 <= Rc2): difference d =
+#   X - P (3), normal dot n.n_X (3), angle compare (1)                  -> 7
+#   per angle-passing pair: beta = n.d (3), orthogonal part r = d - beta n
+#   (3), alpha^2 = |r|^2 (3), u (1), row test (1), alpha = sqrt (1),
+#   fixed-point column V (1), column test (1), fixed-point row U (1)   -> 15
+#   per contributing pair: fraction split (2), product weight (2), the other
+#   weights (3), row and column of the address (4), four shared-memory int32
+#   atomics (4), count (1)                                              -> 16
+# The survey's per-unit estimates (8 per culled pair, ~30 per angle-passing
+# pair, 4 read-modify-writes + ~6 integer ops per in-support pair) give the
+# second figure, roofline["survey_counts"].
+OPS_PER_CULLED = 7
+OPS_PER_ANGLE = 15
+OPS_PER_SUPPORT = 16
+SURVEY_OPS = (8, 30, 10)
+
+
+def alu_ops(n_culled, n_angle, n_support, counts=(OPS_PER_CULLED, OPS_PER_ANGLE, OPS_PER_SUPPORT)):
+    return counts[0] * n_culled + counts[1] * n_angle + counts[2] * n_support
 
 
 # --------------------------------------------------------------------------
@@ -246,14 +257,16 @@ def run_ours(args):
     culled = torch.zeros(m, dtype=torch.int64, device=dev)
     support = torch.zeros(m, dtype=torch.int64, device=dev)
     examined = torch.zeros(m, dtype=torch.int64, device=dev)
+    angle = torch.zeros(m, dtype=torch.int64, device=dev)
     spin.si_generate_probe(mesh, None, m, W, B, cs, sched_probe, out, culled=culled, support=support,
-                           examined=examined, stream=stream)
+                           examined=examined, angle=angle, stream=stream)
     torch.cuda.synchronize()
     spin.si_get_stats(mesh)
     spin.si_mesh_destroy(mesh)
     n_culled = int(culled.sum().item())
     n_support = int(support.sum().item())
     n_examined = int(examined.sum().item())
+    n_angle = int(angle.sum().item())
     examined_per_image = examined.cpu().numpy()
     # measured shared-atomic peak (denominator of the splat roofline)
     atom_peak = spin.si_peak_smem_atomics(0, stream)
@@ -345,14 +358,19 @@ def run_ours(args):
     f_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     sms = sms_count(torch, dev)
     alu_peak = sms * 128 * f_mhz * 1e6  # lane-ops/s at the maximum SM clock
-    ops = OPS_PER_CULLED * n_culled + OPS_PER_SUPPORT * n_support
+    ops = alu_ops(n_culled, n_angle, n_support)
     k_ms = kernel_ms[best]
     achieved = ops / (k_ms / 1e3)
+    achieved_s = alu_ops(n_culled, n_angle, n_support, SURVEY_OPS) / (k_ms / 1e3)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12, "unit": "Tlane-op/s",
                 "frac": achieved / alu_peak, "traffic": _ncu_traffic(c["name"]),
                 "kernel": "spin_kernel (persistent, %s)" % best, "kernel_ms": k_ms,
                 "peak_source": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)" % (sms, f_mhz, peak_src),
-                "ops_per_culled_pair": OPS_PER_CULLED, "ops_per_support_pair": OPS_PER_SUPPORT,
+                "ops_per_culled_pair": OPS_PER_CULLED, "ops_per_angle_pair": OPS_PER_ANGLE,
+                "ops_per_support_pair": OPS_PER_SUPPORT,
+                "survey_counts": {"ops_per_culled_pair": SURVEY_OPS[0], "ops_per_angle_pair": SURVEY_OPS[1],
+                                  "ops_per_support_pair": SURVEY_OPS[2], "achieved": achieved_s / 1e12,
+                                  "frac": achieved_s / alu_peak},
                 "peak_at_clocks": {"%.0f_mhz" % f: {"peak": sms * 128 * f * 1e6 / 1e12,
                                                     "frac": achieved / (sms * 128 * f * 1e6)}
                                    for f in _peak_clocks(peaks, clk)},
@@ -370,6 +388,7 @@ def run_ours(args):
                                   "parallelism": "replicas" if world > 1 else "single GPU"}),
             "culled_pairs_per_s": r["culled_pairs_per_s"], "culled_pairs_per_step": n_culled,
             "support_pairs_per_step": n_support, "examined_pairs_per_step": n_examined,
+            "angle_pairs_per_step": n_angle,
             "stencil_overhead": n_examined / max(1, n_culled),
             "by_schedule": {k: {"images_per_s": v["images_per_s"], "ms_per_step": v["ms_per_step"],
                                 "kernel_ms": v["kernel_ms"], "kernel_ms_quartiles": v["kernel_ms_quartiles"],
@@ -380,12 +399,12 @@ def run_ours(args):
             "gpu_launches": int(timed_launches), "clocks": clk}
     if not args.no_extra:
         from paper_1811_00901_gb300 import workloads as wl
-        ex_steps = max(1, min(args.steps, 3))
+        ex_steps = args.steps
         extra = {}
         extra["sphere-4096-W16"] = bench_single(spin, torch, dev, wl.plain_sphere(), args.steps, args.warmup, flush,
                                                 stream, kinds=("STATIC", "SS", "GSS", "FAC"), pairs=True)
         extra["scene-1M-W64"] = bench_single(spin, torch, dev, wl.large_scene(), ex_steps, args.warmup, flush,
-                                             stream, kinds=("STATIC", "FAC"), pairs=True)
+                                             stream, kinds=("STATIC", "SS", "GSS", "FAC"), pairs=True, e2e=True)
         # probabilistic factoring with sigma / mu of the group cost measured by
         # the probe run (a group's cost follows its candidate stream length)
         cov = _group_cost_cov(examined_per_image)
@@ -411,7 +430,8 @@ def run_ours(args):
             scheds={k: spin.make_schedule(k, binning="NEAREST") for k in ("STATIC", "FAC")})
         del out
         torch.cuda.empty_cache()
-        extra["batched-512-spheres"] = bench_batched(spin, torch, dev, ex_steps, args.warmup, stream)
+        # one batched step writes 140 GB of images (about a second): 7 timed steps
+        extra["batched-512-spheres"] = bench_batched(spin, torch, dev, min(ex_steps, 7), args.warmup, stream)
         torch.cuda.empty_cache()
         extra["serving-64-meshes"] = bench_serving(spin, torch, dev, args.serve_requests, args.serve_pool)
         line["workloads"] = extra
@@ -432,9 +452,13 @@ def run_ours(args):
 # --------------------------------------------------------------------------
 
 def bench_single(spin, torch, dev, c, steps, warmup, flush, stream, kinds=("STATIC", "FAC"), scheds=None,
-                 pairs=False):
-    """One mesh, all its images (or its query list), per rule; kernel time by
-    events.  ``scheds`` (name -> si_schedule) replaces ``kinds`` when given."""
+                 pairs=False, e2e=False):
+    """One mesh, all its images (or its query list), per rule; step and kernel
+    time by events (medians and quartiles over `steps`).  ``scheds`` (name ->
+    si_schedule) replaces ``kinds`` when given.  With ``pairs`` a probe run
+    counts the pairs and the line carries the kernel's ALU roofline; with
+    ``e2e`` the best rule is timed again through si_generate_host from
+    page-locked host buffers."""
     n, m, W, B, cs = c["points"].shape[0], c["m"], c["W"], float(c["bin_size"]), float(c["cos_s"])
     tp = torch.from_numpy(c["points"]).to(dev)
     tn = torch.from_numpy(c["normals"]).to(dev)
@@ -463,28 +487,61 @@ def bench_single(spin, torch, dev, c, steps, warmup, flush, stream, kinds=("STAT
                 times.append(e0.elapsed_time(e1))
                 kms.append(st["kernel_ms"] / max(1, st["kernel_launches"]))
         res[kind] = {"images_per_s": m / (statistics.median(times) / 1e3), "ms_per_step": statistics.median(times),
-                     "kernel_ms": statistics.median(kms)}
-    line = {"images": m, "W": W, "points": n, "by_schedule": res}
+                     "kernel_ms": statistics.median(kms), "kernel_ms_quartiles": _quartiles(kms),
+                     "step_ms_quartiles": _quartiles(times)}
+    line = {"images": m, "W": W, "points": n, "steps": steps, "by_schedule": res}
+    best = max(res, key=lambda k: res[k]["images_per_s"])
     if pairs:
         # pair counts from one probe run (untimed): the kernel's ALU roofline here
         mesh = spin.si_mesh_create(tp, tn, n, stream)
         culled = torch.zeros(m, dtype=torch.int64, device=dev)
         support = torch.zeros(m, dtype=torch.int64, device=dev)
         examined = torch.zeros(m, dtype=torch.int64, device=dev)
+        angle = torch.zeros(m, dtype=torch.int64, device=dev)
         spin.si_generate_probe(mesh, tq, m, W, B, cs, spin.make_schedule("GSS"), out, culled=culled,
-                               support=support, examined=examined, stream=stream)
+                               support=support, examined=examined, angle=angle, stream=stream)
         torch.cuda.synchronize()
         spin.si_get_stats(mesh)
         spin.si_mesh_destroy(mesh)
-        nc, ns, ne = int(culled.sum().item()), int(support.sum().item()), int(examined.sum().item())
-        best = min(res, key=lambda k: res[k]["kernel_ms"])
-        peaks, _ = _measured_peaks()
-        alu_peak = sms_count(torch, dev) * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-        ops = OPS_PER_CULLED * nc + OPS_PER_SUPPORT * ns
-        line.update(culled_pairs_per_step=nc, support_pairs_per_step=ns, examined_pairs_per_step=ne,
-                    stencil_overhead=ne / max(1, nc), culled_pairs_per_s=nc / (res[best]["ms_per_step"] / 1e3),
-                    alu_frac=ops / (res[best]["kernel_ms"] / 1e3) / alu_peak, alu_frac_rule=best)
+        nc, ns, ne, na = (int(t.sum().item()) for t in (culled, support, examined, angle))
+        peaks, src = _measured_peaks()
+        f_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        alu_peak = sms_count(torch, dev) * 128 * f_mhz * 1e6
+        k_s = res[best]["kernel_ms"] / 1e3
+        line.update(culled_pairs_per_step=nc, angle_pairs_per_step=na, support_pairs_per_step=ns,
+                    examined_pairs_per_step=ne, stencil_overhead=ne / max(1, nc),
+                    culled_pairs_per_s=nc / (res[best]["ms_per_step"] / 1e3),
+                    roofline={"bound": "alu", "unit": "Tlane-op/s", "rule": best, "kernel_ms": res[best]["kernel_ms"],
+                              "achieved": alu_ops(nc, na, ns) / k_s / 1e12, "peak": alu_peak / 1e12,
+                              "frac": alu_ops(nc, na, ns) / k_s / alu_peak,
+                              "survey_counts": {"achieved": alu_ops(nc, na, ns, SURVEY_OPS) / k_s / 1e12,
+                                                "frac": alu_ops(nc, na, ns, SURVEY_OPS) / k_s / alu_peak},
+                              "peak_source": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)" % (
+                                  sms_count(torch, dev), f_mhz, src),
+                              "write_gbs": m * W * W * 4 / k_s / 1e9})
     del out
+    if e2e:
+        hp = torch.from_numpy(c["points"]).pin_memory()
+        hn = torch.from_numpy(c["normals"]).pin_memory()
+        hq = None if c["query_idx"] is None else torch.from_numpy(c["query_idx"]).pin_memory()
+        hout = torch.empty((m, W, W), dtype=torch.int32).pin_memory()
+        sched = scheds[best]
+        et = []
+        for k in range(warmup + steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            spin.si_generate_host(hp, hn, n, hq, m, W, B, cs, sched, hout, stream)
+            if k >= warmup:
+                et.append(time.perf_counter() - t0)
+        ms = 1e3 * statistics.median(et)
+        line["e2e"] = {"value": m / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                       "ms_quartiles": _quartiles([1e3 * t for t in et]), "rule": best,
+                       "h2d_bytes_per_step": int(2 * n * 3 * 4 + (0 if hq is None else 4 * m)),
+                       "d2h_bytes_per_step": int(m * W * W * 4),
+                       "api": "si_generate_host (host buffers; mesh/grid build inside; page-locked output "
+                              "written by the kernel)"}
+        del hout
     return line
 
 
@@ -570,7 +627,8 @@ def bench_batched(spin, torch, dev, steps, warmup, stream):
                 if k >= warmup:
                     times.append(e0.elapsed_time(e1))
             res[name] = {"images_per_s": total_images / (statistics.median(times) / 1e3),
-                         "ms_per_step": statistics.median(times)}
+                         "ms_per_step": statistics.median(times), "step_ms_quartiles": _quartiles(times),
+                         "steps": steps}
     finally:
         for mesh in meshes:
             spin.si_mesh_destroy(mesh)

@@ -134,6 +134,8 @@ typedef struct si_probe {
     int32_t *step;       /* scheduling step whose chunk contained the image */
     int64_t *examined;   /* candidate points the kernel streamed for the image (the grid
                             stencil; examined / culled is the culling overhead) */
+    int64_t *angle;      /* candidates (culled set) that pass the support-angle test
+                            n . n_X >= cos S */
 } si_probe;
 
 typedef struct si_stats {

@@ -37,7 +37,8 @@ class si_schedule(ctypes.Structure):
 
 class si_probe(ctypes.Structure):
     _fields_ = [("culled", ctypes.c_void_p), ("cand_hash", ctypes.c_void_p), ("support", ctypes.c_void_p),
-                ("worker", ctypes.c_void_p), ("step", ctypes.c_void_p), ("examined", ctypes.c_void_p)]
+                ("worker", ctypes.c_void_p), ("step", ctypes.c_void_p), ("examined", ctypes.c_void_p),
+                ("angle", ctypes.c_void_p)]
 
 
 class si_stats(ctypes.Structure):
@@ -202,8 +203,9 @@ def si_generate(mesh, query_idx, m, W, bin_size, cos_s, schedule, out, stream=No
 
 
 def si_generate_probe(mesh, query_idx, m, W, bin_size, cos_s, schedule, out, culled=None, cand_hash=None,
-                      support=None, worker=None, step=None, examined=None, stream=None):
-    pr = si_probe(_ptr(culled), _ptr(cand_hash), _ptr(support), _ptr(worker), _ptr(step), _ptr(examined))
+                      support=None, worker=None, step=None, examined=None, angle=None, stream=None):
+    pr = si_probe(_ptr(culled), _ptr(cand_hash), _ptr(support), _ptr(worker), _ptr(step), _ptr(examined),
+                  _ptr(angle))
     _check(load().si_generate_probe(mesh, _ptr(query_idx), int(m), int(W), float(bin_size), float(cos_s), schedule,
                                     _ptr(out), ctypes.byref(pr), _stream_ptr(stream)))
 

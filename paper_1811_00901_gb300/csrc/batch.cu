@@ -395,7 +395,6 @@ void fill_blob(const Plan &p, const std::vector<si_batch_item> &items, const std
         d.invB = 1.0f / it.bin_size;
         d.halfW = 0.5f * (float)it.W;
         d.umax = (float)(it.W - 1);
-        d.amax2 = support_alpha2(it.W, it.bin_size);
         double mag = 0.0;
         for (int a = 0; a < 3; ++a)
             mag = std::max(mag, std::max(std::fabs((double)m->bmin[a]), std::fabs((double)m->bmax[a])));
@@ -408,6 +407,7 @@ void fill_blob(const Plan &p, const std::vector<si_batch_item> &items, const std
             d.p_worker = pr->worker;
             d.p_step = pr->step;
             d.p_examined = pr->examined;
+            d.p_angle = pr->angle;
         }
     }
     int *d_counts = reinterpret_cast<int *>(scratch + p.o_counts);

@@ -116,7 +116,6 @@ struct ItemDesc {
     int W;
     int log2S;             // group = 1 << log2S images
     float invB, halfW, umax, Rc2, Rc, cosS;
-    float amax2;           // fl32(((W-1) B)^2): alpha^2 < amax2 is the column support test
     int units;             // ceil(m / group)
     int perm_is_grid;      // perm holds grid orig_idx (all-points query of the mesh)
     // probes (device, may be null)
@@ -126,6 +125,7 @@ struct ItemDesc {
     int32_t *p_worker;
     int32_t *p_step;
     int64_t *p_examined;
+    int64_t *p_angle;
     // candidate slices per group (>= 1); with more than one, slices add
     // partial images into a zeroed `out` and per-image pair counts into `counts`
     int slices;
@@ -197,12 +197,6 @@ inline int launch_modes_for(int modes, size_t smem_bytes, bool probe) {
 }
 
 // ---------------------------------------------------------- host helpers --
-// Column support threshold: v = alpha / B < W - 1  <=>  alpha^2 < ((W-1) B)^2.
-inline float support_alpha2(int W, float B) {
-    const double a = (double)(W - 1) * (double)B;
-    return (float)(a * a);
-}
-
 Grid *mesh_grid(Mesh *m, float cell, cudaStream_t stream, si_status *st);
 // Candidate threshold of a binning: fl32(R^2 (1 + 1e-5)) with R^2 = h^2 +
 // ((W-1)B)^2 (bilinear, h = W B / 2) or ((W/2 + 1) B)^2 + ((W-1)B)^2 (nearest).

@@ -209,7 +209,6 @@ extern "C" si_status si_generate_noalloc(si_mesh_t mesh, const int32_t *query_id
     d.invB = 1.0f / bin_size;
     d.halfW = 0.5f * (float)W;
     d.umax = (float)(W - 1);
-    d.amax2 = support_alpha2(W, bin_size);
     float mag = 0.0f;
     for (int a = 0; a < 3; ++a) mag = fmaxf(mag, fmaxf(fabsf(me->bmin[a]), fabsf(me->bmax[a])));
     d.margin = (float)(1e-5 * ((double)mag + d.Rc + g->cell_len) + 1e-30);

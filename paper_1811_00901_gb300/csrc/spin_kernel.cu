@@ -29,9 +29,9 @@
 //   alpha^2 = |d - beta n|^2 (the part of d orthogonal to n: Algorithm 1's
 //   |d|^2 - beta^2 for a unit n, without its cancellation near the normal
 //   axis, where FP32 |d|^2 - beta^2 loses alpha to sqrt(eps) |d|);
-//   u = W/2 - beta/B; support test 0 <= u < W-1 and alpha^2 < ((W-1)B)^2
-//   (i.e. v = alpha/B < W-1); v = alpha/B; fixed-point bilinear splat of
-//   weight 65536 with four shared-memory int32 atomics.  The candidate cull
+//   u = W/2 - beta/B; v = alpha/B; support test 0 <= u < W-1 and, on the
+//   fixed-point column V = rn(v 2^16), V < (W-1) 2^16 (v < W-1); fixed-point
+//   bilinear splat of weight 65536 with four shared-memory int32 atomics.  The candidate cull
 //   fl32(|d|^2) <= Rc2 is implied by the support test (every contributing
 //   pair has |d|^2 < R^2 < Rc2), so only probes evaluate it.
 // Images hold (W+1) x (W+1) words per slot: the extra row and column absorb
@@ -89,7 +89,7 @@ constexpr int kHeaderBytes = (sizeof(Header) + 127) / 128 * 128;
 static_assert(sizeof(Header) <= kHeaderBytes, "header too large");
 constexpr int kQueryBytes = 32 * sizeof(QueryInfo);
 constexpr int kRowBytes = 3 * (kMaxRows + 4) * sizeof(int);
-constexpr int kProbeBytes = 4 * 32 * sizeof(int);
+constexpr int kProbeBytes = 5 * 32 * sizeof(int);
 
 // Shared-memory layout of a block: header, queries, stencil rows, probe
 // counters, then per group the tile ring (kStages x tile) and the images.
@@ -159,7 +159,7 @@ __device__ int block_scan_rows(const int *len, int *off, int nr, Header &H) {
 
 // Constants of one item that the pair evaluation needs.
 struct PairConsts {
-    float Rc2, cosS, invB, halfW, umax, amax2, B;
+    float Rc2, cosS, invB, halfW, umax, B;
 };
 
 // Shape of a group's images: compile-time when WT > 0, else runtime.
@@ -213,22 +213,30 @@ __device__ __forceinline__ void eval_pair(const PairDist &pd, const float4 NX, c
     // 0 <= u < W-1 as one unsigned compare of the float bits: non-negative floats
     // order like their bits, negatives (sign bit) and NaN compare above umax; u
     // is never -0 (halfW - beta/B rounds an exact zero to +0)
-    const bool in = live & (ca >= k.cosS) & (__float_as_uint(u) < __float_as_uint(k.umax)) & (a2 < k.amax2);
-    if (PROBE && in) atomicAdd(pc_s, 1);
     // alpha through the approximate square root (zero for a2 = 0, and a2 is a
-    // sum of squares, never negative); the support decision above does not
-    // depend on it, and 16-bit quantisation absorbs its last-bit error
+    // sum of squares, never negative), whose last-bit error the 16-bit
+    // quantisation absorbs.
     float alpha;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(alpha) : "f"(a2));
     // U = rn(u * 2^16): u * 2^16 is exact and below 2^23 (0 <= u < W - 1 <= 127
     // for a contributing pair), so adding 2^23 rounds it to an integer held in
     // the low 23 bits; the low 16 bits are the fraction, the top 16 the row
-    // plus kMagicHi.  V = rn(alpha * (2^16 / B)) the same way, capped at column
-    // W - 1 with a zero fraction: the column test bounds alpha, not the
-    // approximate v, which may exceed W - 1 by a few ulps
+    // plus kMagicHi.  V = rn(alpha * (2^16 / B)) the same way.  For v >= 128
+    // the sum leaves [2^23, 2^24) and its bits only grow (positive floats
+    // order like their bits).
     const uint32_t Ub = __float_as_uint(fmaf(u, 65536.0f, 8388608.0f));
-    const uint32_t Vb = min(__float_as_uint(fmaf(alpha, k.invB * 65536.0f, 8388608.0f)),
-                            0x4B000000u + ((uint32_t)k.umax << 16));
+    const uint32_t Vb = __float_as_uint(fmaf(alpha, k.invB * 65536.0f, 8388608.0f));
+    // The column test is V < (W - 1) 2^16 on those bits: the pair's last
+    // corner column j + 1 = floor(V / 2^16) + 1 stays inside the image.  It
+    // differs from the exact v < W - 1 only for v within 2^-17 of W - 1 or
+    // within the square root's last-bit error of it, pairs well inside the
+    // oracle's boundary band.
+    const bool in = live & (ca >= k.cosS) & (__float_as_uint(u) < __float_as_uint(k.umax)) &
+                    (Vb < 0x4B000000u + ((uint32_t)k.umax << 16));
+    if (PROBE) {
+        if (in) atomicAdd(pc_s, 1);
+        if (live & (pd.d2 <= k.Rc2) & (ca >= k.cosS)) atomicAdd(pc_s + 96, 1);  // angle-passing candidates
+    }
     const uint32_t A = Ub & 0xFFFFu, Bq = Vb & 0xFFFFu;
     const uint32_t w11 = (A * Bq + 32768u) >> 16;
     if (in) {
@@ -262,7 +270,10 @@ __device__ __forceinline__ void eval_pair_nearest(const PairDist &pd, const floa
     const float v = __fdiv_rn(alpha, k.B);
     const float kr = ceilf(u), lc = ceilf(v);
     const bool in = live & (ca >= k.cosS) & (kr >= 0.0f) & (kr <= k.umax) & (lc >= 0.0f) & (lc <= k.umax);
-    if (PROBE && in) atomicAdd(pc_s, 1);
+    if (PROBE) {
+        if (in) atomicAdd(pc_s, 1);
+        if (live & (ca >= k.cosS)) atomicAdd(pc_s + 96, 1);  // live is the cull here: angle-passing candidates
+    }
     if (in) {
         atomicAdd(img_q + (int)kr * sh.row_words() + ((int)lc << sh.log2S()), 1);
         ++cnt;
@@ -370,7 +381,7 @@ struct SmemView {
     Header *H;
     QueryInfo *Q;
     int *row_start, *row_len, *row_off;
-    int *pc_culled, *pc_support, *pc_examined;
+    int *pc_culled, *pc_support, *pc_examined, *pc_angle;
     unsigned *pc_hash;
     float4 *tiles;
     uint32_t dyn_bytes;  // dynamic shared memory of the launch
@@ -408,7 +419,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
     const float ox = it.origin[0], oy = it.origin[1], oz = it.origin[2];
     const float cell = it.cell, inv = it.inv_cell, margin = it.margin;
     const int dx_ = it.dims[0], dy_ = it.dims[1], dz_ = it.dims[2];
-    const PairConsts k{it.Rc2, it.cosS, it.invB, it.halfW, it.umax, it.amax2, it.B};
+    const PairConsts k{it.Rc2, it.cosS, it.invB, it.halfW, it.umax, it.B};
     const float Rc = it.Rc;
     const int slot = lane & (S - 1);
     // candidates per tile: a compile-time constant for the specialised shapes
@@ -455,6 +466,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
         sv.pc_support[tid] = 0;
         sv.pc_hash[tid] = 0;
         sv.pc_examined[tid] = 0;
+        sv.pc_angle[tid] = 0;
     }
     {
         int4 *z4 = reinterpret_cast<int4 *>(img);
@@ -747,6 +759,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
         if (it.p_support) it.p_support[q] = sv.pc_support[tid];
         if (it.p_worker) it.p_worker[q] = (int)blockIdx.x;
         if (it.p_examined) it.p_examined[q] = sv.pc_examined[tid];
+        if (it.p_angle) it.p_angle[q] = sv.pc_angle[tid];
         if (it.p_step) it.p_step[q] = step;
     }
     __syncthreads();
@@ -819,6 +832,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks_for<MODES>()) spin_kernel
     sv.pc_support = sv.pc_culled + 32;
     sv.pc_hash = reinterpret_cast<unsigned *>(sv.pc_support + 32);
     sv.pc_examined = sv.pc_support + 64;
+    sv.pc_angle = sv.pc_support + 96;  // probe counters: the slot's support counter + 96
     sv.tiles = reinterpret_cast<float4 *>(smem + off_tiles());
     Header &H = *sv.H;
     const int tid = threadIdx.x;

@@ -73,23 +73,44 @@ def test_heightfield_100k_full_size():
         assert torch.equal(got, ref), kind
 
 
-def test_scene_1m_w64_sampled():
-    """1M points on 64 objects, 262,144 queries, W=64 (4.3 GB of images); 48
-    sampled images against the oracle."""
+def test_scene_1m_w64_4096_query_subset():
+    """1M points on 64 objects, 262,144 queries, W=64 (4.3 GB of images), in the
+    bench's launch shape; a seeded subset of 4,096 of its images checked in full
+    against the oracle (its image loop spread over the host's cores).  An image
+    outside 1e-4 L1/total is re-checked with the serial oracle, whose boundary
+    flags carry the allowance for pairs FP32 may decide either way."""
     import torch
 
     import paper_1811_00901_gb300 as spin
     c = wl.large_scene()
     out, pr = _run(c, spin.make_schedule("GSS"), probe=True)
     rng = np.random.default_rng(1)
-    sample = np.sort(rng.choice(c["m"], 48, replace=False))
+    sample = np.sort(rng.choice(c["m"], 4096, replace=False))
     imgs = out[torch.from_numpy(sample).to(out.device)].cpu().numpy()
     del out
-    full = {int(s): imgs[k] for k, s in enumerate(sample)}
+    torch.cuda.empty_cache()
+    q = c["query_idx"][sample].astype(np.int32)
+    if oracle.omp_available():
+        ref, sup = oracle.spin_images_omp(c["points"], c["normals"], c["W"], c["bin_size"], c["cos_s"], query_idx=q,
+                                          rule="dynamic")
+    else:
+        ref, sup, _ = oracle.spin_images(c["points"], c["normals"], c["W"], c["bin_size"], c["cos_s"], query_idx=q)
+    g = imgs.astype(np.float64) / 65536.0
+    tot = ref.sum((1, 2))
+    l1 = np.abs(g - ref).sum((1, 2))
+    over = np.nonzero(l1 > 1e-4 * np.maximum(1.0, tot))[0]
+    assert over.size <= 40, "%d of 4096 images above 1e-4 before the flag allowance" % over.size
+    if over.size:
+        full = {int(sample[k]): imgs[k] for k in over}
 
-    class _View:
-        def __getitem__(self, s):
-            return full[int(s)]
+        class _View:
+            def __getitem__(self, s):
+                return full[int(s)]
 
-    compare_with_oracle(_View(), c["points"], c["normals"], c["W"], c["bin_size"], c["cos_s"], c["query_idx"],
-                        sample, support=pr["support"])
+        compare_with_oracle(_View(), c["points"], c["normals"], c["W"], c["bin_size"], c["cos_s"], c["query_idx"],
+                            sample[over], support=pr["support"])
+    # exact totals: 65536 x the contributing count of every sampled image
+    np.testing.assert_array_equal(imgs.astype(np.int64).sum((1, 2)), 65536 * pr["support"][sample])
+    # contributing counts agree but for the rare pair FP32 decides the other way
+    diff = np.abs(pr["support"][sample] - sup)
+    assert diff.max() <= 3 and np.count_nonzero(diff) <= 40

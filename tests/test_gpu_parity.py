@@ -74,6 +74,41 @@ def test_object_scene_w64_query_list():
     np.testing.assert_array_equal(imgs[10], imgs[11])
 
 
+def test_angle_probe_counts_angle_passing_candidates():
+    """The angle probe counts the candidate-set points that pass the support-
+    angle test: support <= angle <= culled for every image, and the count
+    equals an FP64 count (|X - P|^2 <= Rc2 and n . n_X >= cos S) up to the
+    pairs within 1e-5 of either threshold."""
+    import torch
+
+    import paper_1811_00901_gb300 as spin
+    pts, nrm = wl.heightfield(5000, 19)
+    W, B, c = 32, 0.01, float(wl.cos_deg(60.0))
+    dev = torch.device("cuda:0")
+    mesh = spin.si_mesh_create(torch.from_numpy(pts).to(dev), torch.from_numpy(nrm).to(dev))
+    try:
+        m = pts.shape[0]
+        out = torch.empty((m, W, W), dtype=torch.int32, device=dev)
+        pr = {k: torch.full((m,), -1, dtype=torch.int64, device=dev) for k in ("culled", "support", "angle")}
+        spin.si_generate_probe(mesh, None, m, W, B, c, spin.make_schedule("FAC"), out, **pr)
+        torch.cuda.synchronize()
+        spin.si_get_stats(mesh)
+        pr = {k: v.cpu().numpy() for k, v in pr.items()}
+    finally:
+        spin.si_mesh_destroy(mesh)
+    assert np.all(pr["support"] <= pr["angle"]) and np.all(pr["angle"] <= pr["culled"])
+    assert pr["angle"].sum() > pr["support"].sum()
+    rc2 = float(spin.si_candidate_rc2(W, B))
+    P = pts.astype(np.float64)
+    N = nrm.astype(np.float64) / np.linalg.norm(nrm.astype(np.float64), axis=1, keepdims=True)
+    for q in range(0, m, 97):
+        d2 = ((P - P[q]) ** 2).sum(1)
+        dot = N @ N[q]
+        near = (np.abs(d2 - rc2) <= 1e-5 * rc2) | (np.abs(dot - c) <= 1e-5)
+        expect = int(((d2 <= rc2) & (dot >= c)).sum())
+        assert abs(int(pr["angle"][q]) - expect) <= int(near.sum())
+
+
 @pytest.mark.parametrize("W", [16, 32, 64])
 def test_near_axis_needle_and_layers(W):
     """Points on and next to each query's normal axis at distances up to the

@@ -40,13 +40,13 @@ def test_served_results_equal_direct_calls_alone_and_in_the_mix():
     import paper_1811_00901_gb300 as spin
     dev = torch.device("cuda:0")
     meshes = _meshes(torch, spin, dev)
-    srv = spin.si_serve_create(2 << 30, 48)
+    srv = spin.si_serve_create(4 << 30, 64)
     try:
         for mesh, _ in meshes:
             spin.si_serve_add_mesh(srv, mesh)
         rng = np.random.default_rng(7)
         reqs = []
-        for k in range(80):
+        for k in range(200):
             mesh, n = meshes[k % 2]
             m = int(rng.integers(1, 2500))
             W = int(rng.choice([16, 32]))
