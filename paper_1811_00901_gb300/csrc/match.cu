@@ -17,6 +17,7 @@
 #include <mutex>
 
 #include "internal.h"
+#include "match_tc.h"
 
 namespace si {
 namespace {
@@ -72,8 +73,13 @@ cublasHandle_t blas_handle(int dev) {
 }
 
 // ---------------------------------------------------------------- kernels --
-// One warp per image: mean, centred norm (FP64 sums), then (x - mean) / norm
-// (0 for an image without variance).
+// One warp per image: (x - mean) / |x - mean| (0 for an image without
+// variance), without FP64 arithmetic per pixel: the pixel sum is exact in
+// int64, m = the nearest integer to the mean and f = mean - m (|f| <= 1/2);
+// the centred values are (x - m) - f, their squared norm
+// sum (x - m)^2 - K f^2 with the per-lane sums in FP32 (32 terms each for
+// K = 1024, relative error ~2e-6) and the lanes' totals in FP64; the
+// output is FP32 ((x - m) - f) times the reciprocal norm.
 template <typename T>
 __device__ __forceinline__ T to_out(float x);
 template <>
@@ -86,26 +92,33 @@ __device__ __forceinline__ __nv_bfloat16 to_out<__nv_bfloat16>(float x) {
 }
 
 template <typename T>
-__global__ void centre_kernel(const int32_t *__restrict__ img, int64_t n, int K, T *__restrict__ out) {
+__global__ void centre_kernel(const int32_t *__restrict__ img, int64_t n, int K, T *__restrict__ out,
+                              int out_stride) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
         const int32_t *x = img + r * K;
-        double s = 0.0;
-        for (int k = lane; k < K; k += 32) s += (double)x[k];
+        long long s = 0;
+        for (int k = lane; k < K; k += 32) s += x[k];
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
-        const double mean = s / K;
-        double ss = 0.0;
+        // m = round(s / K), halves away from zero; f = s / K - m
+        const long long m = s >= 0 ? (2 * s + K) / (2 * (long long)K) : -((-2 * s + K) / (2 * (long long)K));
+        const double fd = (double)(s - m * (long long)K) / (double)K;
+        const float f = (float)fd;
+        float ssf = 0.0f;
         for (int k = lane; k < K; k += 32) {
-            const double c = (double)x[k] - mean;
-            ss += c * c;
+            const float c = (float)(int)(x[k] - (int)m);
+            ssf = fmaf(c, c, ssf);
         }
+        double ss = (double)ssf;
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, d);
-        const double inv = ss > 0.0 ? 1.0 / sqrt(ss) : 0.0;
-        T *o = out + r * K;
-        for (int k = lane; k < K; k += 32) o[k] = to_out<T>((float)(((double)x[k] - mean) * inv));
+        ss -= (double)K * fd * fd;
+        const float inv = ss > 0.0 ? (float)(1.0 / sqrt(ss)) : 0.0f;
+        T *o = out + r * out_stride;
+        for (int k = lane; k < K; k += 32) o[k] = to_out<T>(((float)(int)(x[k] - (int)m) - f) * inv);
+        for (int k = K + lane; k < out_stride; k += 32) o[k] = to_out<T>(0.0f);  // zero padding of K
     }
 }
 
@@ -261,6 +274,44 @@ __global__ void __launch_bounds__(kTopThreads) topk_kernel(const float *__restri
 constexpr int kMatchMaxK = 16;
 constexpr size_t kTileBytes = (size_t)1 << 30;  // correlation tile scratch bound
 
+// BF16: centred images padded to a multiple of 64 in K, one tensor-core
+// launch with the top-k in its epilogue, a merge of the model ranges.
+si_status match_bf16_tc(const int32_t *scene, int64_t n_scene, const int32_t *model, int64_t n_model, int W, int k,
+                        int32_t *best_idx, float *best_corr, cudaStream_t st, int dev) {
+    const int K = W * W;
+    const int kp = (K + 63) / 64 * 64;
+    const int parts = match_tc_parts(n_scene, n_model, num_sms(dev));
+    __nv_bfloat16 *a = nullptr, *b = nullptr;
+    float *pv = nullptr;
+    int *pi = nullptr;
+    unsigned *err = nullptr;
+    si_status s = dev_alloc((void **)&a, sizeof(__nv_bfloat16) * (size_t)n_scene * kp, st);
+    if (s == SI_OK) s = dev_alloc((void **)&b, sizeof(__nv_bfloat16) * (size_t)n_model * kp, st);
+    if (s == SI_OK) s = dev_alloc((void **)&pv, sizeof(float) * (size_t)parts * n_scene * k, st);
+    if (s == SI_OK) s = dev_alloc((void **)&pi, sizeof(int) * (size_t)parts * n_scene * k, st);
+    if (s == SI_OK) s = dev_alloc((void **)&err, sizeof(unsigned), st);
+    cudaError_t e = cudaSuccess;
+    if (s == SI_OK) {
+        const int blocks = num_sms(dev) * 8;
+        e = cudaMemsetAsync(err, 0, sizeof(unsigned), st);
+        if (e == cudaSuccess) {
+            centre_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(model, n_model, K, b, kp);
+            centre_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(scene, n_scene, K, a, kp);
+            note_launches(2);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess)
+            s = match_tc_launch(a, n_scene, b, n_model, kp, k, parts, pv, pi, err, best_idx, best_corr, st);
+    }
+    if (e != cudaSuccess && s == SI_OK) s = cuda_fail(e, "si_match");
+    dev_free(a, st);
+    dev_free(b, st);
+    dev_free(pv, st);
+    dev_free(pi, st);
+    dev_free(err, st);
+    return s;
+}
+
 }  // namespace
 }  // namespace si
 
@@ -280,8 +331,8 @@ extern "C" si_status si_match(const int32_t *scene, int64_t n_scene, const int32
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0;
     SI_CUDA(cudaGetDevice(&dev));
+    if (precision == SI_MATCH_BF16) return match_bf16_tc(scene, n_scene, model, n_model, W, k, best_idx, best_corr, st, dev);
     cublasHandle_t h = blas_handle(dev);
-    if (!h) return SI_ERR_CUDA;
     const int K = W * W;
     const bool bf16 = precision == SI_MATCH_BF16;
     const size_t esz = bf16 ? sizeof(__nv_bfloat16) : sizeof(float);
@@ -296,9 +347,9 @@ extern "C" si_status si_match(const int32_t *scene, int64_t n_scene, const int32
     if (s == SI_OK) {
         const int blocks = num_sms(dev) * 8;
         if (bf16)
-            centre_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(model, n_model, K, (__nv_bfloat16 *)b);
+            centre_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(model, n_model, K, (__nv_bfloat16 *)b, K);
         else
-            centre_kernel<float><<<blocks, 256, 0, st>>>(model, n_model, K, (float *)b);
+            centre_kernel<float><<<blocks, 256, 0, st>>>(model, n_model, K, (float *)b, K);
         note_launches(1);
         e = cudaGetLastError();
     }
@@ -315,9 +366,9 @@ extern "C" si_status si_match(const int32_t *scene, int64_t n_scene, const int32
         const int nr = (int)std::min<int64_t>(rows, n_scene - r0);
         const int blocks = num_sms(dev) * 8;
         if (bf16)
-            centre_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(scene + r0 * K, nr, K, (__nv_bfloat16 *)a);
+            centre_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(scene + r0 * K, nr, K, (__nv_bfloat16 *)a, K);
         else
-            centre_kernel<float><<<blocks, 256, 0, st>>>(scene + r0 * K, nr, K, (float *)a);
+            centre_kernel<float><<<blocks, 256, 0, st>>>(scene + r0 * K, nr, K, (float *)a, K);
         note_launches(1);
         if ((e = cudaGetLastError()) != cudaSuccess) break;
         // row-major C[nr][n_model] = A[nr][K] . B[n_model][K]^T, i.e. column-major

@@ -1,0 +1,450 @@
+// match_tc.cu -- spin-image matching on the fifth-generation tensor cores:
+// the all-pairs correlation of BF16 centred images as a tcgen05 GEMM whose
+// epilogue keeps each scene image's k best model images, so the correlation
+// tile never leaves the chip.
+//
+// Work decomposition (one CTA per (scene block, model part)):
+//   * a CTA owns 128 scene rows (the MMA's M) and a contiguous range of model
+//     tiles of 256 images (the MMA's N); the model tiles are cut into `parts`
+//     ranges so that the grid fills whole waves of the GPU's SMs;
+//   * warp 0 (one lane) streams 64-element K slices of the scene block and of
+//     the current model tile into a 4-stage shared-memory ring with 2-D TMA
+//     loads (128-byte swizzle), completion on per-stage mbarriers;
+//   * warp 1 allocates 512 TMEM columns (two 128 x 256 FP32 accumulators) and
+//     one of its lanes issues tcgen05.mma (kind::f16, BF16 operands from shared
+//     memory descriptors, FP32 accumulation in TMEM); tcgen05.commit releases a
+//     ring stage when the MMAs reading it are done, and hands a finished
+//     accumulator to the epilogue;
+//   * warps 2-5 read the accumulator out of TMEM (tcgen05.ld, lane i = scene
+//     row i of the block, one thread per row) and offer every value to the
+//     row's running list of the k best (higher value first; model indices
+//     arrive in increasing order, so equal values keep the smaller index);
+//     the second accumulator lets the next tile's MMAs run meanwhile.
+// Each CTA writes its rows' lists; merge_parts_kernel combines the parts.
+//
+// Every mbarrier wait is bounded (kWaitLimitNs of %globaltimer): on expiry the
+// CTA sets the error word, stops issuing, waits (bounded) for the copies and
+// MMAs it has in flight, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cfloat>
+#include <climits>
+#include <mutex>
+
+#include "device_common.cuh"
+#include "internal.h"
+#include "match_tc.h"
+
+namespace si {
+namespace {
+
+constexpr int kBM = 128;             // scene rows per CTA (MMA M)
+constexpr int kBN = 256;             // model images per tile (MMA N)
+constexpr int kBK = 64;              // K elements per ring stage (128 bytes of BF16: one swizzle row)
+constexpr int kStagesTc = 4;         // shared-memory ring depth
+constexpr int kAStageBytes = kBM * kBK * 2;   // 16 KB
+constexpr int kBStageBytes = kBN * kBK * 2;   // 32 KB
+constexpr int kStageBytes = kAStageBytes + kBStageBytes;
+constexpr int kTmemCols = 2 * kBN;   // two FP32 accumulators of 128 lanes x 256 columns
+constexpr int kTcThreads = 192;      // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kTcSmem = 1024 + kStagesTc * kStageBytes + 256;
+
+struct TcBarriers {
+    uint64_t full[kStagesTc];
+    uint64_t empty[kStagesTc];
+    uint64_t tfull[2];
+    uint64_t tempty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+};
+static_assert(sizeof(TcBarriers) <= 256, "barrier block");
+
+// ---- PTX wrappers (tcgen05, TMA) ----
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor of a K-major BF16 tile written by TMA with
+// the 128-byte swizzle: rows of 128 bytes, 8-row atoms 1024 bytes apart (the
+// stride byte offset); the leading byte offset is unused for this layout.
+// Fields: start address >> 4 (bits 0-13), leading offset >> 4 (16-29),
+// stride offset >> 4 (32-45), descriptor version 1 (46-47), swizzle mode
+// 2 = 128-byte (61-63).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
+// A and B (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at
+// bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
+                            ((uint32_t)(kBM >> 4) << 24);
+
+// Bounded wait on an mbarrier phase; false (and the abort flag set) on expiry.
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!*abort_flag) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitLimitNs) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return false;
+}
+
+// Inserts (x, j) into a descending list of k (strictly better than its k-th,
+// which the caller checked); returns the new k-th value.
+__device__ __noinline__ float topk_push(float *v, int *ix, int k, float x, int j) {
+    int q = k - 1;
+    while (q > 0 && v[q - 1] < x) {
+        v[q] = v[q - 1];
+        ix[q] = ix[q - 1];
+        --q;
+    }
+    v[q] = x;
+    ix[q] = j;
+    return v[k - 1];
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    match_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                    const int n_scene, const int n_model, const int k_slices, const int tiles, const int parts,
+                    const int k, float *__restrict__ part_v, int *__restrict__ part_i, unsigned *err) {
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw = smem_addr(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;  // 128-byte swizzle atoms need 1024-byte alignment
+    unsigned char *const sbase = smem_raw + (base - raw);
+    TcBarriers &B = *reinterpret_cast<TcBarriers *>(sbase + kStagesTc * kStageBytes);
+    volatile int *abort_flag = &B.abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // part-major order: the CTAs resident at one time work on the same model
+    // range, so its tiles come from DRAM once and from L2 after that
+    const int mblocks = (n_scene + kBM - 1) / kBM;
+    const int part = blockIdx.x / mblocks, mb = blockIdx.x - part * mblocks;
+    const int t0 = (int)((int64_t)tiles * part / parts), t1 = (int)((int64_t)tiles * (part + 1) / parts);
+    const int ntile = t1 - t0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStagesTc; ++s) {
+            mbar_init(&B.full[s], 1);
+            mbar_init(&B.empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&B.tfull[b], 1);
+            mbar_init(&B.tempty[b], 4);
+        }
+        mbar_init(&B.drain, 1);
+        B.abort = 0;
+        fence_mbar_init();
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_b)) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&B.tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = B.tmem_base;
+
+    if (warp == 0) {
+        // ---- producer: K slices of the scene block and of each model tile
+        if (lane == 0) {
+            int it = 0, issued = 0;
+            for (int t = 0; t < ntile && !*abort_flag; ++t) {
+                const int ncol0 = (t0 + t) * kBN;
+                for (int ks = 0; ks < k_slices; ++ks, ++it) {
+                    const int s = it % kStagesTc;
+                    const uint32_t ph = (uint32_t)(it / kStagesTc) & 1u;
+                    if (!tc_wait(&B.empty[s], ph ^ 1u, abort_flag)) break;
+                    const uint32_t a_dst = base + s * kStageBytes, b_dst = a_dst + kAStageBytes;
+                    mbar_arrive_expect_tx(&B.full[s], (uint32_t)kStageBytes);
+                    tma_load_2d(a_dst, &map_a, ks * kBK, mb * kBM, smem_addr(&B.full[s]));
+                    tma_load_2d(b_dst, &map_b, ks * kBK, ncol0, smem_addr(&B.full[s]));
+                    ++issued;
+                }
+            }
+            if (*abort_flag) {
+                // let every copy this thread issued land before the CTA goes
+                for (int j = (issued > kStagesTc ? issued - kStagesTc : 0); j < issued; ++j)
+                    mbar_wait_bounded(&B.full[j % kStagesTc], (uint32_t)(j / kStagesTc) & 1u, kWaitLimitNs);
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            int it = 0;
+            for (int t = 0; t < ntile && !*abort_flag; ++t) {
+                const int b = t & 1;
+                const uint32_t tph = (uint32_t)(t >> 1) & 1u;
+                if (!tc_wait(&B.tempty[b], tph ^ 1u, abort_flag)) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * kBN);
+                bool ok = true;
+                for (int ks = 0; ks < k_slices; ++ks, ++it) {
+                    const int s = it % kStagesTc;
+                    const uint32_t ph = (uint32_t)(it / kStagesTc) & 1u;
+                    if (!tc_wait(&B.full[s], ph, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a_addr = base + s * kStageBytes, b_addr = a_addr + kAStageBytes;
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk)  // four K = 16 MMAs, 32 bytes apart in the swizzle row
+                        tc_mma(d, smem_desc_sw128(a_addr + 32u * kk), smem_desc_sw128(b_addr + 32u * kk), kIdesc,
+                               (ks | kk) != 0 ? 1u : 0u);
+                    tc_commit(smem_addr(&B.empty[s]));  // the stage is free once these MMAs are done
+                }
+                if (!ok) break;
+                tc_commit(smem_addr(&B.tfull[b]));  // the accumulator is complete
+            }
+            // every MMA this thread issued has completed once this arrives
+            tc_commit(smem_addr(&B.drain));
+            mbar_wait_bounded(&B.drain, 0u, kWaitLimitNs);
+        }
+    } else {
+        // ---- epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31, one scene row per thread
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        float v[kMatchTcMaxK];
+        int ix[kMatchTcMaxK];
+        for (int q = 0; q < kMatchTcMaxK; ++q) {
+            v[q] = -FLT_MAX;
+            ix[q] = INT_MAX;
+        }
+        float thr = -FLT_MAX;
+        for (int t = 0; t < ntile; ++t) {
+            const int b = t & 1;
+            const uint32_t tph = (uint32_t)(t >> 1) & 1u;
+            if (!tc_wait(&B.tfull[b], tph, abort_flag)) break;
+            tc_fence_after();
+            const int ncol0 = (t0 + t) * kBN;
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kBN);
+            for (int c = 0; c < kBN / 32; ++c) {
+                float x[32];
+                tc_ld32(taddr + (uint32_t)(c * 32), x);
+                if (c == kBN / 32 - 1) {
+                    // all of this buffer is in registers: hand it back to the MMA warp
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&B.tempty[b]);
+                }
+                const int j0 = ncol0 + c * 32;
+                const int valid = n_model - j0;  // columns past the last model image hold zeros
+                if (valid >= 32) {
+#pragma unroll
+                    for (int u = 0; u < 32; ++u)
+                        if (x[u] > thr) thr = topk_push(v, ix, k, x[u], j0 + u);
+                } else {
+                    for (int u = 0; u < valid; ++u)
+                        if (x[u] > thr) thr = topk_push(v, ix, k, x[u], j0 + u);
+                }
+            }
+        }
+        const int grow = mb * kBM + row;
+        if (grow < n_scene && !*abort_flag) {
+            const int64_t o = ((int64_t)part * n_scene + grow) * k;
+            for (int q = 0; q < k; ++q) {
+                part_v[o + q] = v[q];
+                part_i[o + q] = ix[q];
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+    if (threadIdx.x == 0 && *abort_flag) atomicOr(err, 1u);
+}
+
+// a before b: higher value, equal values by smaller index
+__device__ __forceinline__ bool better_vi(float va, int ia, float vb, int ib) {
+    return va > vb || (va == vb && ia < ib);
+}
+
+// One thread per scene row: the k best of the parts' sorted lists.
+__global__ void merge_parts_kernel(const float *__restrict__ part_v, const int *__restrict__ part_i, int n_scene,
+                                   int parts, int k, const unsigned *err, int32_t *__restrict__ best_idx,
+                                   float *__restrict__ best_val) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_scene) return;
+    if (*err) {  // some CTA gave up a bounded wait: the call's lists are void
+        for (int q = 0; q < k; ++q) {
+            best_idx[(int64_t)r * k + q] = -2;
+            best_val[(int64_t)r * k + q] = 0.0f;
+        }
+        return;
+    }
+    int head[kMatchTcMaxParts];
+    for (int p = 0; p < parts; ++p) head[p] = 0;
+    for (int q = 0; q < k; ++q) {
+        int bp = -1;
+        float bv = 0.0f;
+        int bi = INT_MAX;
+        for (int p = 0; p < parts; ++p) {
+            if (head[p] >= k) continue;
+            const int64_t o = ((int64_t)p * n_scene + r) * k + head[p];
+            const float x = part_v[o];
+            const int xi = part_i[o];
+            if (bp < 0 || better_vi(x, xi, bv, bi)) {
+                bp = p;
+                bv = x;
+                bi = xi;
+            }
+        }
+        ++head[bp];
+        best_val[(int64_t)r * k + q] = bv;
+        best_idx[(int64_t)r * k + q] = bi == INT_MAX ? -1 : bi;
+    }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// dependency on the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn(si_status *st) {
+    static std::mutex mu;
+    static EncodeTiledFn fn = nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) {
+            *st = e != cudaSuccess ? cuda_fail(e, "cuTensorMapEncodeTiled entry point") : SI_ERR_CUDA;
+            if (e == cudaSuccess) set_error("si_match: cuTensorMapEncodeTiled is not available");
+            return nullptr;
+        }
+        fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    *st = SI_OK;
+    return fn;
+}
+
+// Row-major BF16 [rows][kp] as a 2-D tensor map with (64 x box_rows) boxes.
+si_status make_map(CUtensorMap *m, const void *ptr, int64_t rows, int kp, int box_rows) {
+    si_status st;
+    EncodeTiledFn fn = encode_fn(&st);
+    if (!fn) return st;
+    const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("si_match: cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return SI_ERR_CUDA;
+    }
+    return SI_OK;
+}
+
+}  // namespace
+
+int match_tc_parts(int64_t n_scene, int64_t n_model, int sms) {
+    const int64_t mblocks = (n_scene + kBM - 1) / kBM;
+    const int64_t tiles = (n_model + kBN - 1) / kBN;
+    // the smallest number of model parts (at most one per 4 tiles, at most
+    // kMatchTcMaxParts) whose grid loses the least to a partly filled last wave
+    int best = 1;
+    double best_eff = -1.0;
+    for (int p = 1; p <= kMatchTcMaxParts && (p == 1 || tiles / p >= 4); ++p) {
+        const int64_t ctas = mblocks * p;
+        const int64_t waves = (ctas + sms - 1) / sms;
+        const double eff = (double)ctas / (double)(waves * sms);
+        if (eff > best_eff + 1e-3) {
+            best_eff = eff;
+            best = p;
+        }
+        if (eff > 0.97) break;
+    }
+    return best;
+}
+
+si_status match_tc_launch(const __nv_bfloat16 *a, int64_t n_scene, const __nv_bfloat16 *b, int64_t n_model, int kp,
+                          int k, int parts, float *part_v, int *part_i, unsigned *err, int32_t *best_idx,
+                          float *best_val, cudaStream_t st) {
+    if (kp % kBK != 0 || k < 1 || k > kMatchTcMaxK || parts < 1 || parts > kMatchTcMaxParts || n_scene < 1 ||
+        n_model < 1 || n_scene > INT32_MAX || n_model > INT32_MAX) {
+        set_error("si_match: internal tensor-core launch arguments");
+        return SI_ERR_INVALID;
+    }
+    CUtensorMap ma, mbm;
+    si_status s = make_map(&ma, a, n_scene, kp, kBM);
+    if (s == SI_OK) s = make_map(&mbm, b, n_model, kp, kBN);
+    if (s != SI_OK) return s;
+    static std::mutex attr_mu;
+    static bool attr_done[128] = {};
+    int dev = 0;
+    SI_CUDA(cudaGetDevice(&dev));
+    {
+        std::lock_guard<std::mutex> lk(attr_mu);
+        if (dev >= 0 && dev < 128 && !attr_done[dev]) {
+            SI_CUDA(cudaFuncSetAttribute(match_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+            attr_done[dev] = true;
+        }
+    }
+    const int64_t mblocks = (n_scene + kBM - 1) / kBM;
+    const int tiles = (int)((n_model + kBN - 1) / kBN);
+    match_tc_kernel<<<(unsigned)(mblocks * parts), kTcThreads, kTcSmem, st>>>(
+        ma, mbm, (int)n_scene, (int)n_model, kp / kBK, tiles, parts, k, part_v, part_i, err);
+    note_launches(1);
+    SI_CUDA(cudaGetLastError());
+    merge_parts_kernel<<<(unsigned)((n_scene + 255) / 256), 256, 0, st>>>(part_v, part_i, (int)n_scene, parts, k,
+                                                                          err, best_idx, best_val);
+    note_launches(1);
+    SI_CUDA(cudaGetLastError());
+    return SI_OK;
+}
+
+}  // namespace si

@@ -86,3 +86,85 @@ def test_invalid_arguments():
     for args in [(a, 2, a, 2, 8, 4, 0), (a, 2, a, 2, 8, 0, 0), (a, 2, a, 2, 8, 17, 0), (a, 2, a, 2, 8, 2, 5)]:
         with pytest.raises(spin.SpinError):
             spin.si_match(*args, i, v)
+
+
+def _balanced_images(rng, n, W):
+    """Images with exactly half of their W^2 pixels at 0 and half at one
+    positive amplitude (its own per image): centred and scaled to unit length
+    every pixel is +-1/W, exact in BF16 for W a power of two, whatever the
+    rounding of the centring arithmetic.  Every correlation is then a multiple
+    of 2/W^2, exact in FP32 accumulation."""
+    K = W * W
+    imgs = np.zeros((n, K), np.int32)
+    for r in range(n):
+        imgs[r, rng.permutation(K)[: K // 2]] = int(rng.integers(1, 30000)) * 65536 // 7
+    return imgs.reshape(n, W, W)
+
+
+def _run_bf16(scene, model, W, k):
+    import torch
+
+    import paper_1811_00901_gb300 as spin
+    dev = torch.device("cuda:0")
+    n_scene, n_model = len(scene), len(model)
+    idx = torch.full((n_scene, k), -3, dtype=torch.int32, device=dev)
+    val = torch.zeros((n_scene, k), dtype=torch.float32, device=dev)
+    spin.si_match(torch.from_numpy(scene).to(dev), n_scene, torch.from_numpy(model).to(dev), n_model, W, k, "BF16",
+                  idx, val)
+    torch.cuda.synchronize()
+    return idx.cpu().numpy(), val.cpu().numpy()
+
+
+@pytest.mark.parametrize("W,k,n_scene,n_model", [(16, 16, 257, 1025), (32, 5, 200, 3000), (64, 3, 129, 600),
+                                                 (32, 7, 1000, 20000)])
+def test_tensor_core_exact_products_and_ties(W, k, n_scene, n_model):
+    """BF16 matching on the tensor cores with operands that BF16 holds exactly
+    (balanced two-level images): every reported value equals the FP64
+    correlation exactly, and each list is exactly the k best, equal values by
+    smaller model index (the images repeat, so there are many exact ties).
+    Scene and model counts are ragged against the 128 x 256 tile."""
+    rng = np.random.default_rng(W * 1000 + k)
+    base = _balanced_images(rng, max(8, n_model // 3), W)
+    model = base[rng.integers(0, len(base), n_model)]           # many duplicates: exact ties
+    scene = base[rng.integers(0, len(base), n_scene)].copy()
+    K = W * W
+    for r in range(n_scene):                                      # move a few pixel pairs: near matches
+        flat = scene[r].reshape(-1)
+        on, off = np.nonzero(flat)[0], np.nonzero(flat == 0)[0]
+        for _ in range(int(rng.integers(0, 4))):
+            a, b = rng.choice(on), rng.choice(off)
+            flat[a], flat[b] = 0, flat[a] if flat[a] else flat[on[0]]
+            on, off = np.nonzero(flat)[0], np.nonzero(flat == 0)[0]
+    idx, val = _run_bf16(scene, model, W, k)
+    r = match.correlations(scene, model)
+    # the exact correlations are multiples of 2/K; the FP64 ones carry ~1e-16
+    # of rounding, which must neither show in the values nor break ties
+    steps = np.round(r * K / 2)
+    assert np.all(np.abs(r * K / 2 - steps) < 1e-9)
+    exact = steps * (2.0 / K)
+    ref_idx = np.lexsort((np.broadcast_to(np.arange(n_model), exact.shape), -exact), axis=1)[:, :k]
+    ref_val = np.take_along_axis(exact, ref_idx, axis=1)
+    assert np.any(ref_val[:, :-1] == ref_val[:, 1:])  # the lists do hold exact ties
+    np.testing.assert_array_equal(val, ref_val.astype(np.float32))
+    np.testing.assert_array_equal(idx, ref_idx)
+
+
+def test_tensor_core_padded_width():
+    """W = 5: W^2 = 25 pixels padded to one 64-element K slice with zeros; the
+    reported values are within the BF16 bound of the FP64 correlations and
+    the lists are valid and sorted."""
+    rng = np.random.default_rng(5)
+    W, k, n_scene, n_model = 5, 4, 130, 300
+    model = ((rng.random((n_model, W, W)) < 0.5) * rng.integers(0, 40 * 65536, (n_model, W, W))).astype(np.int32)
+    scene = model[rng.integers(0, n_model, n_scene)].copy()
+    scene += ((rng.random(scene.shape) < 0.1) * rng.integers(0, 65536 * 8, scene.shape)).astype(np.int32)
+    idx, val = _run_bf16(scene, model, W, k)
+    r = match.correlations(scene, model)
+    tol = 2.0 ** -8 + 1e-4
+    for i in range(n_scene):
+        assert len(set(idx[i])) == k and (idx[i] >= 0).all()
+        assert np.all(np.diff(val[i]) <= 0)
+        assert np.all(np.abs(val[i] - r[i, idx[i]]) <= tol)
+        out = np.ones(n_model, bool)
+        out[idx[i]] = False
+        assert r[i, out].max() <= r[i, idx[i, k - 1]] + 2 * tol
