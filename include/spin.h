@@ -375,18 +375,28 @@ si_status si_debug_fail_allocs(int64_t skip, int64_t count);
  * N = W^2, the similarity measure of spin-image matching (Johnson and Hebert,
  * 1999, the recognition work the paper cites); an image without variance
  * correlates 0.  Over all bins R is the dot product of the centred, unit-length
- * images, so the all-pairs step is one dense contraction, run through cuBLAS
- * (loaded at first use): SI_MATCH_BF16 on the tensor cores (BF16 operands,
- * FP32 accumulation: |R error| <= 2^-8 from rounding the unit-length operands
- * to BF16, plus FP32 accumulation error, about W^2 x 2^-24 at worst),
- * SI_MATCH_FP32 as an FP32 GEMM (accumulation error only).
+ * images, so the all-pairs step is one dense contraction; it runs on the
+ * tensor cores (this library's tcgen05 kernel, FP32 accumulation) with the
+ * k-best selection in the kernel's epilogue, so the correlation matrix is
+ * never stored:
+ *   SI_MATCH_BF16 -- the centred images rounded to BF16: |R error| <= 2^-8
+ *     from the operand rounding plus the accumulation error below;
+ *   SI_MATCH_FP32 -- each centred value split into three BF16 terms (24
+ *     significant bits) and the six products of FP32 accuracy summed in one
+ *     GEMM over 6 W^2: |R error| within the accumulation error below.
+ *   Accumulation: each 16-term step enters the FP32 accumulator with up to one
+ *   unit in its last place, i.e. about (K / 16) 2^-23 for K = W^2 (BF16) or
+ *   6 W^2 (FP32) terms at worst.
  *   scene : device int32[n_scene][W][W], model : device int32[n_model][W][W]
  *           (images as si_generate writes them);
  *   best_idx, best_corr : device [n_scene][k], highest R first, equal values
  *           by smaller model index; 1 <= k <= min(16, n_model).
- * Scratch comes from the stream-ordered pool (at most ~1 GiB of correlation
- * tile plus the centred images).  Stream-ordered; argument errors are
- * synchronous.  The paper has no counterpart (its subject is generation). */
+ * Scratch comes from the stream-ordered pool (the centred images, 2 bytes per
+ * value in BF16 and 12 in FP32 mode, plus the k-best lists of the model
+ * ranges).  Stream-ordered; argument errors are synchronous.  A bounded wait
+ * of the kernel that gives up (which a correct run never meets) makes every
+ * best_idx of the call -2.  The paper has no counterpart (its subject is
+ * generation). */
 typedef enum si_match_precision { SI_MATCH_FP32 = 0, SI_MATCH_BF16 = 1 } si_match_precision;
 si_status si_match(const int32_t *scene, int64_t n_scene, const int32_t *model, int64_t n_model, int32_t W,
                    int32_t k, int32_t precision, int32_t *best_idx, float *best_corr, si_stream stream);

@@ -101,7 +101,7 @@ def _balanced_images(rng, n, W):
     return imgs.reshape(n, W, W)
 
 
-def _run_bf16(scene, model, W, k):
+def _run_bf16(scene, model, W, k, precision="BF16"):
     import torch
 
     import paper_1811_00901_gb300 as spin
@@ -109,15 +109,16 @@ def _run_bf16(scene, model, W, k):
     n_scene, n_model = len(scene), len(model)
     idx = torch.full((n_scene, k), -3, dtype=torch.int32, device=dev)
     val = torch.zeros((n_scene, k), dtype=torch.float32, device=dev)
-    spin.si_match(torch.from_numpy(scene).to(dev), n_scene, torch.from_numpy(model).to(dev), n_model, W, k, "BF16",
+    spin.si_match(torch.from_numpy(scene).to(dev), n_scene, torch.from_numpy(model).to(dev), n_model, W, k, precision,
                   idx, val)
     torch.cuda.synchronize()
     return idx.cpu().numpy(), val.cpu().numpy()
 
 
-@pytest.mark.parametrize("W,k,n_scene,n_model", [(16, 16, 257, 1025), (32, 5, 200, 3000), (64, 3, 129, 600),
-                                                 (32, 7, 1000, 20000)])
-def test_tensor_core_exact_products_and_ties(W, k, n_scene, n_model):
+@pytest.mark.parametrize("W,k,n_scene,n_model,precision", [(16, 16, 257, 1025, "BF16"), (32, 5, 200, 3000, "BF16"),
+                                                           (64, 3, 129, 600, "BF16"), (32, 7, 1000, 20000, "BF16"),
+                                                           (32, 5, 300, 2000, "FP32"), (16, 3, 130, 700, "FP32")])
+def test_tensor_core_exact_products_and_ties(W, k, n_scene, n_model, precision):
     """BF16 matching on the tensor cores with operands that BF16 holds exactly
     (balanced two-level images): every reported value equals the FP64
     correlation exactly, and each list is exactly the k best, equal values by
@@ -135,7 +136,7 @@ def test_tensor_core_exact_products_and_ties(W, k, n_scene, n_model):
             a, b = rng.choice(on), rng.choice(off)
             flat[a], flat[b] = 0, flat[a] if flat[a] else flat[on[0]]
             on, off = np.nonzero(flat)[0], np.nonzero(flat == 0)[0]
-    idx, val = _run_bf16(scene, model, W, k)
+    idx, val = _run_bf16(scene, model, W, k, precision)
     r = match.correlations(scene, model)
     # the exact correlations are multiples of 2/K; the FP64 ones carry ~1e-16
     # of rounding, which must neither show in the values nor break ties
