@@ -423,6 +423,9 @@ def run_ours(args):
         h["over_static"] = {k: v["images_per_s"] / h["by_schedule"]["STATIC"]["images_per_s"]
                             for k, v in h["by_schedule"].items()}
         extra["heterogeneous-heightfield-100k-W32"] = h
+        extra["trace-heightfield-100k-W32"] = bench_trace(spin, torch, dev, c, shape, stream)
+        extra["trace-heterogeneous-heightfield-100k-W32"] = bench_trace(
+            spin, torch, dev, c, shape, stream, het=dict(num_workers=P, slow_workers=P // 2, slowdown=3.0))
         extra["matching-16k-vs-100k-W32"] = bench_matching(spin, torch, dev, c, ex_steps, args.warmup, stream)
         # Algorithm 1's own nearest-bin count on the bench workload
         extra["nearest-bin-heightfield-100k-W32"] = bench_single(
@@ -545,6 +548,47 @@ def bench_single(spin, torch, dev, c, steps, warmup, flush, stream, kinds=("STAT
     return line
 
 
+def bench_trace(spin, torch, dev, c, shape, stream, het=None):
+    """Each worker's finishing time under STATIC and the dynamic rules (the GPU
+    analogue of the per-rank finishing times of the paper's Fig. 2): one traced
+    run per rule (si_generate_traced, %globaltimer at every claim); times from
+    the first claim's start.  With ``het`` the heterogeneity emulation's
+    schedule fields are applied."""
+    n, m, W, B, cs = c["points"].shape[0], c["m"], c["W"], float(c["bin_size"]), float(c["cos_s"])
+    tp = torch.from_numpy(c["points"]).to(dev)
+    tn = torch.from_numpy(c["normals"]).to(dev)
+    out = torch.empty((m, W, W), dtype=torch.int32, device=dev)
+    mesh = spin.si_mesh_create(tp, tn, n, stream)
+    res = {}
+    try:
+        for kind in ("STATIC", "SS", "GSS", "FAC"):
+            sched = spin.make_schedule(kind, **shape, **(het or {}))
+            P = spin.si_default_workers(W, sched) if not het else het["num_workers"]
+            claims = torch.zeros((200000, 4), dtype=torch.int64, device=dev)
+            count = torch.zeros(1, dtype=torch.int64, device=dev)
+            spin.si_generate(mesh, None, m, W, B, cs, sched, out, stream)  # grid and warm-up
+            spin.si_generate_traced(mesh, None, m, W, B, cs, sched, out, claims, count, stream)
+            torch.cuda.synchronize()
+            nc = min(int(count.item()), claims.shape[0])
+            tr = claims[:nc].cpu().numpy()
+            t0 = tr[:, 2].min()
+            finish = np.zeros(P)
+            busy = np.zeros(P)
+            for w, _, a, b in tr:
+                finish[w] = max(finish[w], (b - t0) / 1e6)
+                busy[w] += (b - a) / 1e6
+            res[kind] = {"claims": nc, "workers": int(P), "finish_ms_max": float(finish.max()),
+                         "finish_ms_mean": float(finish.mean()), "finish_ms_min": float(finish.min()),
+                         "finish_quartiles_ms": _quartiles(finish),
+                         "imbalance": float((finish.max() - finish.mean()) / finish.max()),
+                         "busy_ms_mean": float(busy.mean())}
+        spin.si_get_stats(mesh)
+    finally:
+        spin.si_mesh_destroy(mesh)
+    return {"workload": c["name"], "by_schedule": res,
+            "note": "imbalance = (latest - mean finishing time) / latest finishing time of the workers"}
+
+
 def bench_matching(spin, torch, dev, c, steps, warmup, stream, n_scene=16384, k=5):
     """Spin-image matching: n_scene images of a rigidly moved copy of the bench
     mesh against all images of the mesh (correlation over all bins, k best)."""
@@ -569,7 +613,8 @@ def bench_matching(spin, torch, dev, c, steps, warmup, stream, n_scene=16384, k=
     val = torch.empty((n_scene, k), dtype=torch.float32, device=dev)
     peaks, src = _measured_peaks()
     res = {}
-    for prec in ("BF16", "FP32"):
+    kp = (W * W + 63) // 64 * 64
+    for prec, ksplit in (("BF16", 1), ("FP32", 6)):
         times = []
         for it in range(warmup + steps):
             torch.cuda.synchronize()
@@ -582,15 +627,24 @@ def bench_matching(spin, torch, dev, c, steps, warmup, stream, n_scene=16384, k=
             if it >= warmup:
                 times.append(e0.elapsed_time(e1))
         ms = statistics.median(times)
+        # the correlation's algorithmic flops, and the BF16 tensor-core flops
+        # the call executes (K padded to 64; FP32 mode: six BF16 products per term)
         flops = 2.0 * n_scene * m * W * W
-        res[prec] = {"ms": ms, "correlations_per_s": n_scene * m / (ms / 1e3), "tflops": flops / (ms / 1e3) / 1e12}
-        if prec == "BF16" and "bf16_tflops" in peaks:
-            res[prec]["frac_of_bf16_peak"] = res[prec]["tflops"] / float(peaks["bf16_tflops"])
-    # how many scene images found their own point of the unmoved mesh first
-    hit = float((idx[:, 0].long().cpu() == q.long().cpu()).float().mean().item())
+        tc_flops = 2.0 * n_scene * m * kp * ksplit
+        res[prec] = {"ms": ms, "ms_quartiles": _quartiles(times), "steps": steps,
+                     "correlations_per_s": n_scene * m / (ms / 1e3), "tflops": flops / (ms / 1e3) / 1e12,
+                     "tensor_tflops": tc_flops / (ms / 1e3) / 1e12,
+                     # how many scene images found their own point of the unmoved mesh first
+                     "top1_is_the_same_point": float((idx[:, 0].long().cpu() == q.long().cpu()).float().mean().item())}
+        if "bf16_tflops" in peaks:
+            res[prec]["roofline"] = {"bound": "tensor", "achieved": res[prec]["tensor_tflops"],
+                                     "peak": float(peaks["bf16_tflops"]), "unit": "TFLOP/s",
+                                     "frac": res[prec]["tensor_tflops"] / float(peaks["bf16_tflops"]),
+                                     "peak_source": "measured bf16_tflops (burst; whole call: centring + GEMM "
+                                                    "with fused top-k + merge)"}
     del model, scene
-    return {"scene_images": n_scene, "model_images": m, "W": W, "k": k, "by_precision": res,
-            "top1_is_the_same_point": hit, "peak_source": src}
+    return {"scene_images": n_scene, "model_images": m, "W": W, "k": k, "by_precision": res, "peak_source": src,
+            "kernel": "match_tc_kernel (tcgen05, TMEM accumulators, top-k fused in the epilogue)"}
 
 
 def bench_batched(spin, torch, dev, steps, warmup, stream):

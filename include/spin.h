@@ -144,7 +144,8 @@ typedef struct si_stats {
     int32_t overflow;       /* 1 if some pixel of some image exceeded INT32_MAX */
     int32_t timeout;        /* 1 if a bounded device wait gave up (images incomplete) */
     int32_t bad_query;      /* 1 if a query index was outside [0, n) (that image is not computed) */
-    int32_t reserved;
+    int32_t bad_input;      /* 1 if a device input point of the mesh had a non-finite coordinate or a
+                               zero normal (si_mesh_create checks host inputs itself) */
     int64_t grid_cells;     /* cells of the most recently built grid */
     int64_t kernel_launches;/* timed spin-kernel launches (see si_set_timing) */
     double kernel_ms;       /* their summed device time, CUDA events on the launch stream */
@@ -165,10 +166,13 @@ typedef struct si_batch_item {
  * si_mesh_create -- copy an oriented-point set into the library (the input
  * replication of Sec. 3, "the input data is replicated").
  *   points, normals : host or device, float[n][3] (x, y, z), n >= 1.
- *   Normals are normalised in FP32; a zero or non-finite normal or a
- *   non-finite coordinate is SI_ERR_INVALID.
- * Synchronises `stream` once (to read back the bounding box).  The mesh is
- * bound to the current device. */
+ *   Normals are normalised in FP32.  A zero or non-finite normal or a
+ *   non-finite coordinate is SI_ERR_INVALID: here, synchronously, for host
+ *   inputs; for device inputs the check runs on the device and si_get_stats
+ *   reports it (bad_input; the mesh's images are then unspecified).
+ * Stream-ordered: nothing is read back, the call does not synchronise (the
+ * bounding box and the grids derived from it stay on the device).  The mesh
+ * is bound to the current device. */
 si_status si_mesh_create(const float *points, const float *normals, int64_t n,
                          si_stream stream, si_mesh_t *out_mesh);
 
@@ -211,6 +215,24 @@ si_status si_generate(si_mesh_t mesh, const int32_t *query_idx, int64_t m, int32
 si_status si_generate_probe(si_mesh_t mesh, const int32_t *query_idx, int64_t m, int32_t W,
                             float bin_size, float cos_support_angle, si_schedule schedule,
                             int32_t *out, const si_probe *probe, si_stream stream);
+
+/* Per-claim trace of the image loop (the GPU analogue of the per-rank finishing
+ * times of Sec. 2.1, Fig. 2): one entry per scheduling claim a worker made. */
+typedef struct si_trace {
+    int64_t *claims;            /* device [capacity][4]: worker (thread block), scheduling step,
+                                   start and end of the claim's work (ns of the GPU's global
+                                   timer, %globaltimer; a slow worker of the heterogeneity
+                                   emulation includes its idle) */
+    int64_t capacity;           /* entries `claims` holds */
+    unsigned long long *count;  /* device, zeroed by the caller: claims made (entries past
+                                   `capacity` are counted and dropped) */
+} si_trace;
+
+/* si_generate with the claim trace (see si_trace); images are unchanged.
+ * SI_ERR_INVALID if trace is NULL or its buffers are missing. */
+si_status si_generate_traced(si_mesh_t mesh, const int32_t *query_idx, int64_t m, int32_t W,
+                             float bin_size, float cos_support_angle, si_schedule schedule,
+                             int32_t *out, const si_trace *trace, si_stream stream);
 
 /* si_generate_batched -- many meshes, each with its own W, B, cos S, queries
  * and output, in ONE persistent launch: the concatenation of every item's

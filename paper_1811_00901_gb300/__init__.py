@@ -14,4 +14,4 @@ from ._binding import (  # noqa: F401
     si_reset_stats, si_serve_add_mesh, si_serve_create, si_serve_destroy, si_serve_poll, si_serve_release,
     si_serve_result, si_serve_submit, si_serve_wait, si_set_timing, si_tune_clear, si_tune_load, si_tune_lookup,
     si_tune_mesh, si_tune_save, si_version, si_kernel_launches, si_peak_smem_atomics, device_view,
-    si_alloc_stats, si_debug_fail_allocs)
+    si_alloc_stats, si_debug_fail_allocs, si_generate_traced)

@@ -43,9 +43,13 @@ class si_probe(ctypes.Structure):
 
 class si_stats(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_int64), ("images", ctypes.c_int64), ("overflow", ctypes.c_int32),
-                ("timeout", ctypes.c_int32), ("bad_query", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("timeout", ctypes.c_int32), ("bad_query", ctypes.c_int32), ("bad_input", ctypes.c_int32),
                 ("grid_cells", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("kernel_ms", ctypes.c_double)]
+
+
+class si_trace(ctypes.Structure):
+    _fields_ = [("claims", ctypes.c_void_p), ("capacity", ctypes.c_int64), ("count", ctypes.c_void_p)]
 
 
 class si_batch_item(ctypes.Structure):
@@ -64,6 +68,8 @@ _SIGNATURES = {
                     ctypes.c_int),
     "si_generate_probe": ([_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_float, si_schedule,
                            _P, ctypes.POINTER(si_probe), _P], ctypes.c_int),
+    "si_generate_traced": ([_P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_float, si_schedule,
+                            _P, ctypes.POINTER(si_trace), _P], ctypes.c_int),
     "si_generate_batched": ([ctypes.POINTER(si_batch_item), ctypes.c_int32, ctypes.POINTER(si_schedule), _P],
                             ctypes.c_int),
     "si_generate_host": ([_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_float,
@@ -208,6 +214,14 @@ def si_generate_probe(mesh, query_idx, m, W, bin_size, cos_s, schedule, out, cul
                   _ptr(angle))
     _check(load().si_generate_probe(mesh, _ptr(query_idx), int(m), int(W), float(bin_size), float(cos_s), schedule,
                                     _ptr(out), ctypes.byref(pr), _stream_ptr(stream)))
+
+
+def si_generate_traced(mesh, query_idx, m, W, bin_size, cos_s, schedule, out, claims, count, stream=None):
+    """si_generate with the per-claim trace: claims is a device int64 [capacity, 4] tensor
+    (worker, step, start ns, end ns), count a zeroed device uint64/int64 [1] tensor."""
+    tr = si_trace(_ptr(claims), int(claims.shape[0]), _ptr(count))
+    _check(load().si_generate_traced(mesh, _ptr(query_idx), int(m), int(W), float(bin_size), float(cos_s), schedule,
+                                     _ptr(out), ctypes.byref(tr), _stream_ptr(stream)))
 
 
 def batch_items(items):

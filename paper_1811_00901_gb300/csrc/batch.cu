@@ -27,9 +27,7 @@ struct SortItem {
     int64_t qbase;  // first query of the item in the concatenated query space
     int64_t hbase;  // first histogram bin of the item
     int n_points;
-    float origin[3];
-    float inv;
-    int dims[3];
+    const GridGeom *geom;
 };
 
 __device__ __forceinline__ int find_item(const int64_t *qbase, int nitems, int64_t g) {
@@ -49,10 +47,11 @@ __device__ __forceinline__ int query_cell(const SortItem &s, int64_t q) {
     if ((unsigned)src >= (unsigned)s.n_points) src = 0;  // reported by the spin kernel
     const int sp = s.sorted_pos[src];
     const float4 p = s.pn[2 * (int64_t)sp];
-    const int cx = cell_coord(p.x, s.origin[0], s.inv, s.dims[0]);
-    const int cy = cell_coord(p.y, s.origin[1], s.inv, s.dims[1]);
-    const int cz = cell_coord(p.z, s.origin[2], s.inv, s.dims[2]);
-    return (cz * s.dims[1] + cy) * s.dims[0] + cx;
+    const GridGeom &g = *s.geom;
+    const int cx = cell_coord(p.x, g.origin[0], g.inv_cell, g.dims[0]);
+    const int cy = cell_coord(p.y, g.origin[1], g.inv_cell, g.dims[1]);
+    const int cz = cell_coord(p.z, g.origin[2], g.inv_cell, g.dims[2]);
+    return (cz * g.dims[1] + cy) * g.dims[0] + cx;
 }
 
 __global__ void qsort_count_kernel(const SortItem *__restrict__ items, const int64_t *__restrict__ qbase,
@@ -315,16 +314,12 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
         s.n_points = (int)m->n;
         s.qbase = p->qtot;
         s.hbase = p->htot;
-        for (int d = 0; d < 3; ++d) {
-            s.origin[d] = g->origin[d];
-            s.dims[d] = g->dims[d];
-        }
-        s.inv = g->inv_cell;
+        s.geom = g->geom;
         p->sort_of[k] = (int)p->sitems.size();
         p->sitems.push_back(s);
         p->sqbase.push_back(p->qtot);
         p->qtot += it.m;
-        p->htot += g->ncell;
+        p->htot += g->ncell_cap;  // the device geometry's cells fit within the cap
     }
     if (p->htot + 1 > INT32_MAX || p->qtot > INT32_MAX) {
         set_error("query sort too large for one call");
@@ -373,12 +368,7 @@ void fill_blob(const Plan &p, const std::vector<si_batch_item> &items, const std
         d.pn = g->pn;
         d.cell_start = g->cell_start;
         d.sorted_pos = g->sorted_pos;
-        for (int a = 0; a < 3; ++a) {
-            d.origin[a] = g->origin[a];
-            d.dims[a] = g->dims[a];
-        }
-        d.cell = g->cell_len;
-        d.inv_cell = g->inv_cell;
+        d.geom = g->geom;
         if (p.sort_of[k] < 0) {
             d.perm = g->orig_idx;
             d.perm_is_grid = 1;
@@ -395,10 +385,6 @@ void fill_blob(const Plan &p, const std::vector<si_batch_item> &items, const std
         d.invB = 1.0f / it.bin_size;
         d.halfW = 0.5f * (float)it.W;
         d.umax = (float)(it.W - 1);
-        double mag = 0.0;
-        for (int a = 0; a < 3; ++a)
-            mag = std::max(mag, std::max(std::fabs((double)m->bmin[a]), std::fabs((double)m->bmax[a])));
-        d.margin = (float)(1e-5 * (mag + d.Rc + g->cell_len) + 1e-30);
         const si_probe *pr = probes.empty() ? nullptr : probes[k];
         if (pr) {
             d.p_culled = pr->culled;
@@ -434,7 +420,7 @@ void fill_blob(const Plan &p, const std::vector<si_batch_item> &items, const std
 // Device commands of a planned batch on `stream` (also what a graph captures).
 // Returns the number of kernels recorded in *kernels.
 si_status record_batch(const Plan &p, const std::vector<si_batch_item> &items, char *scratch, bool probe,
-                       cudaStream_t stream, int *kernels) {
+                       cudaStream_t stream, int *kernels, const si_trace *trace = nullptr) {
     int nk = 0;
     cudaError_t e = cudaMemsetAsync(scratch + p.o_ctr, 0, sizeof(LaunchCounters), stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");
@@ -493,6 +479,11 @@ si_status record_batch(const Plan &p, const std::vector<si_batch_item> &items, c
     const int blocks = p.all_static ? p.nsteps : p.workers;
     a.slow_workers = std::min(p.slow_workers, blocks);
     a.slowdown = p.slowdown;
+    if (trace) {
+        a.trace = trace->claims;
+        a.trace_cap = trace->capacity;
+        a.trace_count = trace->count;
+    }
     launch_spin_kernel(a, p.all_static ? p.nsteps : p.workers, p.smem, stream);
     ++nk;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "spin kernel launch");
@@ -586,7 +577,8 @@ std::vector<char> batch_key(const std::vector<si_batch_item> &items, const std::
 }  // namespace
 
 si_status enqueue_batch(const std::vector<si_batch_item> &items, const std::vector<si_schedule> &scheds,
-                        const std::vector<const si_probe *> &probes, cudaStream_t stream, int forced_workers) {
+                        const std::vector<const si_probe *> &probes, cudaStream_t stream, int forced_workers,
+                        const si_trace *trace) {
     bool probe = false;
     for (auto *pr : probes)
         if (pr) probe = true;
@@ -602,7 +594,7 @@ si_status enqueue_batch(const std::vector<si_batch_item> &items, const std::vect
     if (st == SI_OK) {
         TimedRegion tr(reinterpret_cast<Mesh *>(items[0].mesh), stream);
         int nk = 0;
-        st = record_batch(p, items, scratch, probe, stream, &nk);
+        st = record_batch(p, items, scratch, probe, stream, &nk, trace);
         tr.end(stream);
         note_launches(nk);
         if (st == SI_OK) note_calls(items);

@@ -105,6 +105,19 @@ static si_schedule norm_sched(si_schedule s) { return s; }
 
 extern "C" {
 
+si_status si_generate_traced(si_mesh_t mesh, const int32_t *query_idx, int64_t m, int32_t W, float bin_size,
+                             float cos_support_angle, si_schedule schedule, int32_t *out, const si_trace *trace,
+                             si_stream stream) {
+    if (!trace || !trace->claims || !trace->count || trace->capacity < 0) {
+        set_error("si_generate_traced: need claims, count and capacity >= 0");
+        return SI_ERR_INVALID;
+    }
+    si_batch_item it{mesh, query_idx, m, W, bin_size, cos_support_angle, out};
+    std::vector<si_batch_item> items{it};
+    std::vector<si_schedule> sc{norm_sched(schedule)};
+    return enqueue_batch(items, sc, {}, (cudaStream_t)stream, 0, trace);
+}
+
 si_status si_generate_probe(si_mesh_t mesh, const int32_t *query_idx, int64_t m, int32_t W, float bin_size,
                             float cos_support_angle, si_schedule schedule, int32_t *out, const si_probe *probe,
                             si_stream stream) {
@@ -173,7 +186,8 @@ si_status si_generate_host(const float *points, const float *normals, int64_t n,
     }
     cudaStream_t s = (cudaStream_t)stream;
     si_mesh_t mesh = nullptr;
-    si_status st = si_mesh_create(points, normals, n, stream, &mesh);
+    // the inputs are checked on the device; si_get_stats below reports a bad point
+    si_status st = mesh_create(points, normals, n, stream, &mesh, false);
     if (st != SI_OK) return st;
     int32_t *d_q = nullptr, *d_out = nullptr;
     const size_t img_words = (size_t)W * W;
@@ -309,6 +323,12 @@ si_status si_get_stats(si_mesh_t mesh, si_stats *out) {
     SI_CUDA(cudaDeviceSynchronize());
     unsigned flags = 0;
     SI_CUDA(cudaMemcpy(&flags, m->flags, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    int cells = 0;  // the most recently built grid's cells (its geometry lives on the device)
+    {
+        std::lock_guard<std::mutex> lk(m->mu);
+        if (!m->grids.empty())
+            SI_CUDA(cudaMemcpy(&cells, &m->grids.back()->geom->ncell, sizeof(int), cudaMemcpyDeviceToHost));
+    }
     {
         std::lock_guard<std::mutex> lk(m->mu);
         for (auto &pe : m->pending_events) {
@@ -323,13 +343,14 @@ si_status si_get_stats(si_mesh_t mesh, si_stats *out) {
         m->pending_events.clear();
         out->calls = m->calls;
         out->images = m->images;
-        out->grid_cells = m->last_cells;
+        out->grid_cells = cells;
         out->kernel_launches = m->timed_launches;
         out->kernel_ms = m->timed_ms;
     }
     out->overflow = (flags & kFlagOverflow) ? 1 : 0;
     out->timeout = (flags & kFlagTimeout) ? 1 : 0;
     out->bad_query = (flags & kFlagBadQuery) ? 1 : 0;
+    out->bad_input = (flags & kFlagBadInput) ? 1 : 0;
     if (out->overflow) {
         set_error("a pixel exceeded INT32_MAX");
         return SI_ERR_OVERFLOW;
@@ -338,9 +359,17 @@ si_status si_get_stats(si_mesh_t mesh, si_stats *out) {
         set_error("a bounded device wait gave up");
         return SI_ERR_TIMEOUT;
     }
+    if (flags & kFlagBounds) {
+        set_error("an index check of the bounds-checking build failed (the access was skipped)");
+        return SI_ERR_CUDA;
+    }
     if (flags & kFlagLaunch) {
         set_error("internal error: a spin-kernel launch had less shared memory than its layout");
         return SI_ERR_CUDA;
+    }
+    if (out->bad_input) {
+        set_error("a point of the mesh had a non-finite coordinate or a zero normal (its images are unspecified)");
+        return SI_ERR_INVALID;
     }
     if (out->bad_query) {
         set_error("a query index was outside [0, n); its image was not written");

@@ -63,16 +63,28 @@ constexpr unsigned kFlagOverflow = 1u;
 constexpr unsigned kFlagTimeout = 2u;
 constexpr unsigned kFlagBadQuery = 4u;  // a query index outside [0, n): its image is left unwritten
 constexpr unsigned kFlagLaunch = 8u;    // the kernel's shared-memory layout did not fit its launch: no work done
+constexpr unsigned kFlagBadInput = 16u; // a device input point had a non-finite coordinate or a zero normal
+constexpr unsigned kFlagBounds = 32u;   // SI_DEBUG_BOUNDS builds: an index check failed (the access was skipped)
 
 // ------------------------------------------------------------------- grid --
+// Geometry of a uniform grid over the mesh's bounding box, computed on the
+// device (grid_geom_kernel) from the bounding box the mesh's ingest kernel
+// left there, so that building and using a grid needs no host round trip.
+struct GridGeom {
+    float origin[3];  // the bounding box's minimum corner
+    float cell_len;   // cell edge (>= the requested edge when the grid was coarsened)
+    float inv_cell;   // 1 / cell_len
+    float mag;        // largest |coordinate| of the bounding box (stencil margin)
+    int dims[3];
+    int ncell;        // dims[0] dims[1] dims[2] <= the grid's ncell_cap
+};
+
 // A uniform grid over the mesh's bounding box; points counting-sorted by cell.
 struct Grid {
-    float cell = 0.f, inv_cell = 0.f;  // cache key (requested edge), 1 / actual edge
-    float cell_len = 0.f;               // actual edge (>= cell when the grid was coarsened)
-    float origin[3] = {0, 0, 0};
-    int dims[3] = {1, 1, 1};
-    int64_t ncell = 0;
-    int *cell_start = nullptr;  // [ncell + 1]
+    float cell = 0.f;           // cache key: the requested edge
+    int64_t ncell_cap = 0;      // cells the arrays are sized for (the device geometry stays within it)
+    GridGeom *geom = nullptr;   // device
+    int *cell_start = nullptr;  // [ncell_cap + 1]
     float4 *pn = nullptr;       // [2n]: (x, y, z, orig index bits), (nx, ny, nz, 0)
     int *sorted_pos = nullptr;  // [n]: original index -> sorted position
     int *orig_idx = nullptr;    // [n]: sorted position -> original index
@@ -84,12 +96,12 @@ struct Mesh {
     int64_t n = 0;
     float4 *pos = nullptr;  // original order, w = 0
     float4 *nrm = nullptr;  // original order, normalised
-    float bmin[3] = {0, 0, 0}, bmax[3] = {0, 0, 0};
+    unsigned *bbox_keys = nullptr;  // device [8]: order-preserving keys of min xyz, max xyz
     std::vector<Grid *> grids;
     unsigned *flags = nullptr;  // device word: kFlag*
     cudaEvent_t ready = nullptr;
     std::mutex mu;
-    int64_t calls = 0, images = 0, last_cells = 0;
+    int64_t calls = 0, images = 0;
     // timing
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending_events;
     int64_t timed_launches = 0;
@@ -107,10 +119,7 @@ struct ItemDesc {
     const int *perm;       // [m] grid-ordered query t -> query slot q; null: identity order
     int32_t *out;          // [m][W][W]
     unsigned *flags;
-    float origin[3];
-    float cell, inv_cell;
-    int dims[3];
-    float margin;          // stencil safety margin (length units)
+    const GridGeom *geom;  // the grid's geometry (device)
     int64_t m;
     int n_points;          // mesh size (query indices are checked against it)
     int W;
@@ -170,6 +179,10 @@ struct LaunchArgs {
     const int *awf_batch = nullptr;  // FAC2 chunk of batch j, j < awf_nbatch
     int awf_nbatch = 0;
     int min_chunk = 1;
+    // claim trace (si_generate_traced): [trace_cap][4] worker, step, start, end
+    int64_t *trace = nullptr;
+    int64_t trace_cap = 0;
+    unsigned long long *trace_count = nullptr;
 };
 
 // Tile-ring discipline of a group shape: groups of <= 4 images run a producer
@@ -197,7 +210,11 @@ inline int launch_modes_for(int modes, size_t smem_bytes, bool probe) {
 }
 
 // ---------------------------------------------------------- host helpers --
+si_status mesh_create(const float *points, const float *normals, int64_t n, si_stream stream, si_mesh_t *out_mesh,
+                      bool check_host);
 Grid *mesh_grid(Mesh *m, float cell, cudaStream_t stream, si_status *st);
+// Cells a grid of a mesh of n points may have (the coarsening bound).
+int64_t grid_cell_cap(int64_t n);
 // Candidate threshold of a binning: fl32(R^2 (1 + 1e-5)) with R^2 = h^2 +
 // ((W-1)B)^2 (bilinear, h = W B / 2) or ((W/2 + 1) B)^2 + ((W-1)B)^2 (nearest).
 float candidate_rc2(int W, float bin_size, int binning);
@@ -221,7 +238,7 @@ si_status check_item(const si_batch_item &it, const si_schedule &sc, int dev);
 // Enqueue the generation of a batch of items (host-validated) on `stream`.
 si_status enqueue_batch(const std::vector<si_batch_item> &items, const std::vector<si_schedule> &scheds,
                         const std::vector<const si_probe *> &probes, cudaStream_t stream,
-                        int forced_workers);
+                        int forced_workers, const si_trace *trace = nullptr);
 // The same for batched calls through the CUDA-graph cache (capture once,
 // replay for identical batches); the legacy default stream goes direct.
 si_status enqueue_batch_graph(const std::vector<si_batch_item> &items, const std::vector<si_schedule> &scheds,

@@ -5,6 +5,7 @@
 // float4.  Grids are built lazily per cell size and cached on the mesh: a
 // counting sort of the points by cell (cell ids -> histogram -> exclusive
 // scan -> scatter), giving cell_start[] and the points in cell order.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -19,7 +20,7 @@ namespace {
 __global__ void mesh_ingest_kernel(const float *__restrict__ pts, const float *__restrict__ nrm, int64_t n,
                                    float4 *__restrict__ pos, float4 *__restrict__ nrm_out,
                                    unsigned *__restrict__ keys /* [6]: min xyz, max xyz */,
-                                   unsigned *__restrict__ bad) {
+                                   unsigned *__restrict__ flags) {
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     unsigned my_bad = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -32,6 +33,9 @@ __global__ void mesh_ingest_kernel(const float *__restrict__ pts, const float *_
         if (!ok) {
             my_bad = 1;
             l2 = 1.0f;
+            x = isfinite(x) ? x : 0.0f;  // keep the bounding box finite
+            y = isfinite(y) ? y : 0.0f;
+            z = isfinite(z) ? z : 0.0f;
         }
         float inv = __fdiv_rn(1.0f, __fsqrt_rn(l2));
         pos[i] = make_float4(x, y, z, 0.0f);
@@ -60,23 +64,67 @@ __global__ void mesh_ingest_kernel(const float *__restrict__ pts, const float *_
                 atomicMax(&keys[3 + k], float_key(hi[k]));
             }
         }
-        if (my_bad) atomicOr(bad, 1u);
+        if (my_bad) atomicOr(flags, kFlagBadInput);
     }
 }
 
-struct GridView {
-    float o0, o1, o2, inv;
-    int d0, d1, d2;
-};
-
-__device__ __forceinline__ int cell_of(const GridView &g, float4 p) {
-    int cx = cell_coord(p.x, g.o0, g.inv, g.d0);
-    int cy = cell_coord(p.y, g.o1, g.inv, g.d1);
-    int cz = cell_coord(p.z, g.o2, g.inv, g.d2);
-    return (cz * g.d1 + cy) * g.d0 + cx;
+// Decodes an order-preserving key (float_key) back to the float.
+__device__ __forceinline__ float key_float(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-__global__ void grid_count_kernel(const float4 *__restrict__ pos, int64_t n, GridView g, int *__restrict__ hist) {
+// The grid's geometry from the mesh's bounding box: cells of edge `cell`
+// (coarsened by 1.25x until at most `cap` cells cover the box), origin at the
+// box's minimum corner.  One thread.
+__global__ void grid_geom_kernel(const unsigned *__restrict__ keys, float cell, int64_t cap, GridGeom *g) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double lo[3], hi[3];
+    const bool empty = keys[0] == 0xffffffffu;  // no point reached the box (cannot happen for n >= 1)
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = empty ? 0.0 : (double)key_float(keys[k]);
+        hi[k] = empty ? 0.0 : (double)key_float(keys[3 + k]);
+    }
+    double cellv = cell;
+    int dims[3] = {1, 1, 1};
+    int64_t ncell = 1;
+    for (int guard = 0; guard < 64; ++guard) {
+        ncell = 1;
+        for (int k = 0; k < 3; ++k) {
+            double d = ceil((hi[k] - lo[k]) / cellv);
+            if (d < 1) d = 1;
+            if (d > (1 << 20)) d = 1 << 20;
+            dims[k] = (int)d;
+            ncell *= dims[k];
+        }
+        if (ncell <= cap) break;
+        cellv *= 1.25;
+    }
+    if (ncell > cap) {  // unreachable for finite boxes; one cell keeps every index in range
+        dims[0] = dims[1] = dims[2] = 1;
+        ncell = 1;
+    }
+    double mag = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        g->origin[k] = (float)lo[k];
+        g->dims[k] = dims[k];
+        mag = fmax(mag, fmax(fabs(lo[k]), fabs(hi[k])));
+    }
+    g->cell_len = (float)cellv;
+    g->inv_cell = (float)(1.0 / cellv);
+    g->mag = (float)mag;
+    g->ncell = (int)ncell;
+}
+
+__device__ __forceinline__ int cell_of(const GridGeom &g, float4 p) {
+    int cx = cell_coord(p.x, g.origin[0], g.inv_cell, g.dims[0]);
+    int cy = cell_coord(p.y, g.origin[1], g.inv_cell, g.dims[1]);
+    int cz = cell_coord(p.z, g.origin[2], g.inv_cell, g.dims[2]);
+    return (cz * g.dims[1] + cy) * g.dims[0] + cx;
+}
+
+__global__ void grid_count_kernel(const float4 *__restrict__ pos, int64_t n, const GridGeom *__restrict__ gp,
+                                  int *__restrict__ hist) {
+    const GridGeom g = *gp;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         atomicAdd(&hist[cell_of(g, pos[i])], 1);
     }
@@ -87,8 +135,9 @@ __global__ void grid_count_kernel(const float4 *__restrict__ pos, int64_t n, Gri
 // cell is whatever the atomics give.  Every result of the library is
 // independent of that order (integer accumulation).
 __global__ void grid_scatter_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ nrm, int64_t n,
-                                    GridView g, int *__restrict__ cursor, float4 *__restrict__ pn,
+                                    const GridGeom *__restrict__ gp, int *__restrict__ cursor, float4 *__restrict__ pn,
                                     int *__restrict__ sorted_pos, int *__restrict__ orig_idx) {
+    const GridGeom g = *gp;
     const int lane = threadIdx.x & 31;
     for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) - lane; base < n;
          base += (int64_t)gridDim.x * blockDim.x) {
@@ -124,6 +173,7 @@ int grid_blocks(int64_t n) {
 // allocates in microseconds); callers free them with no work pending.
 void free_grid(Grid *g, cudaStream_t stream) {
     if (!g) return;
+    dev_free(g->geom, stream);
     dev_free(g->cell_start, stream);
     dev_free(g->pn, stream);
     dev_free(g->sorted_pos, stream);
@@ -156,6 +206,11 @@ float candidate_rc2(int W, float bin_size, int binning) {
     return (float)((h * h + r * r) * (1.0 + 1e-5));
 }
 
+// At most 8 cells per point (and 2^24): a grid whose requested cells would
+// outnumber that is coarsened; the bound sizes the cell array before the
+// geometry is known on the host.
+int64_t grid_cell_cap(int64_t n) { return std::min<int64_t>(int64_t(1) << 24, 8 * n + 4096); }
+
 float grid_cell_for(const Mesh *m, int W, float bin, int grid_div) {
     (void)m;
     double R = std::sqrt((double)si_candidate_rc2(W, bin));
@@ -177,34 +232,14 @@ Grid *mesh_grid(Mesh *m, float cell, cudaStream_t stream, si_status *st) {
             }
             return g;
         }
-    // build a new grid
-    double ext[3], cellv = cell;
-    int64_t ncell = 0;
-    int dims[3];
-    for (int guard = 0; guard < 64; ++guard) {
-        ncell = 1;
-        for (int k = 0; k < 3; ++k) {
-            ext[k] = (double)m->bmax[k] - (double)m->bmin[k];
-            double d = std::ceil(ext[k] / cellv);
-            if (d < 1) d = 1;
-            if (d > (1 << 20)) d = 1 << 20;
-            dims[k] = (int)d;
-            ncell *= dims[k];
-        }
-        if (ncell <= (int64_t(1) << 24) && ncell <= 64 * m->n + 4096) break;
-        cellv *= 1.25;
-    }
+    // build a new grid: its geometry comes from the bounding box on the device
+    const int64_t cap = grid_cell_cap(m->n);
     Grid *g = new Grid();
-    g->cell = cell;  // cache key stays the requested cell
-    g->inv_cell = (float)(1.0 / cellv);
-    g->cell_len = (float)cellv;
-    for (int k = 0; k < 3; ++k) {
-        g->origin[k] = m->bmin[k];
-        g->dims[k] = dims[k];
-    }
-    g->ncell = ncell;
+    g->cell = cell;
+    g->ncell_cap = cap;
     cudaError_t e = cudaSuccess;
-    *st = dev_alloc((void **)&g->cell_start, sizeof(int) * (ncell + 1), stream);
+    *st = dev_alloc((void **)&g->geom, sizeof(GridGeom), stream);
+    if (*st == SI_OK) *st = dev_alloc((void **)&g->cell_start, sizeof(int) * (cap + 1), stream);
     if (*st == SI_OK) *st = dev_alloc((void **)&g->pn, sizeof(float4) * 2 * m->n, stream);
     if (*st == SI_OK) *st = dev_alloc((void **)&g->sorted_pos, sizeof(int) * m->n, stream);
     if (*st == SI_OK) *st = dev_alloc((void **)&g->orig_idx, sizeof(int) * m->n, stream);
@@ -216,24 +251,25 @@ Grid *mesh_grid(Mesh *m, float cell, cudaStream_t stream, si_status *st) {
         free_grid(g, stream);
         return nullptr;
     }
-    GridView gv{g->origin[0], g->origin[1], g->origin[2], g->inv_cell, dims[0], dims[1], dims[2]};
     int *cursor = nullptr;
     do {
         e = cudaStreamWaitEvent(stream, m->ready, 0);
         if (e != cudaSuccess) break;
-        e = cudaMemsetAsync(g->cell_start, 0, sizeof(int) * (ncell + 1), stream);
+        grid_geom_kernel<<<1, 32, 0, stream>>>(m->bbox_keys, cell, cap, g->geom);
+        note_launches(1);
+        e = cudaMemsetAsync(g->cell_start, 0, sizeof(int) * (cap + 1), stream);
         if (e != cudaSuccess) break;
-        grid_count_kernel<<<grid_blocks(m->n), 256, 0, stream>>>(m->pos, m->n, gv, g->cell_start);
+        grid_count_kernel<<<grid_blocks(m->n), 256, 0, stream>>>(m->pos, m->n, g->geom, g->cell_start);
         note_launches(1);
         e = cudaGetLastError();
         if (e != cudaSuccess) break;
-        *st = scan_exclusive(g->cell_start, g->cell_start, ncell + 1, stream);
+        *st = scan_exclusive(g->cell_start, g->cell_start, cap + 1, stream);
         if (*st != SI_OK) break;
-        *st = dev_alloc((void **)&cursor, sizeof(int) * ncell, stream);
+        *st = dev_alloc((void **)&cursor, sizeof(int) * cap, stream);
         if (*st != SI_OK) break;
-        e = cudaMemcpyAsync(cursor, g->cell_start, sizeof(int) * ncell, cudaMemcpyDeviceToDevice, stream);
+        e = cudaMemcpyAsync(cursor, g->cell_start, sizeof(int) * cap, cudaMemcpyDeviceToDevice, stream);
         if (e != cudaSuccess) break;
-        grid_scatter_kernel<<<grid_blocks(m->n), 256, 0, stream>>>(m->pos, m->nrm, m->n, gv, cursor, g->pn,
+        grid_scatter_kernel<<<grid_blocks(m->n), 256, 0, stream>>>(m->pos, m->nrm, m->n, g->geom, cursor, g->pn,
                                                                   g->sorted_pos, g->orig_idx);
         note_launches(1);
         e = cudaGetLastError();
@@ -248,7 +284,6 @@ Grid *mesh_grid(Mesh *m, float cell, cudaStream_t stream, si_status *st) {
         return nullptr;
     }
     m->grids.push_back(g);
-    m->last_cells = ncell;
     return g;
 }
 
@@ -256,10 +291,11 @@ Grid *mesh_grid(Mesh *m, float cell, cudaStream_t stream, si_status *st) {
 
 using namespace si;
 
-extern "C" {
-
-si_status si_mesh_create(const float *points, const float *normals, int64_t n, si_stream stream,
-                         si_mesh_t *out_mesh) {
+namespace si {
+// si_mesh_create; with check_host false, host inputs are checked on the device
+// like device inputs (for callers that read si_get_stats before returning).
+si_status mesh_create(const float *points, const float *normals, int64_t n, si_stream stream,
+                      si_mesh_t *out_mesh, bool check_host) {
     if (!out_mesh) {
         set_error("si_mesh_create: out_mesh is NULL");
         return SI_ERR_INVALID;
@@ -269,76 +305,83 @@ si_status si_mesh_create(const float *points, const float *normals, int64_t n, s
         set_error("si_mesh_create: need non-NULL points/normals and 1 <= n <= 2^30 (n = %lld)", (long long)n);
         return SI_ERR_INVALID;
     }
+    const bool dev_p = is_device_pointer(points), dev_n = is_device_pointer(normals);
+    // host inputs are checked here, synchronously; device inputs by the ingest
+    // kernel, which flags the mesh (si_get_stats reports it)
+    for (int64_t i = 0; check_host && !dev_p && i < 3 * n; ++i)
+        if (!std::isfinite(points[i])) {
+            set_error("si_mesh_create: coordinate %lld is not finite", (long long)i);
+            return SI_ERR_INVALID;
+        }
+    for (int64_t i = 0; check_host && !dev_n && i < n; ++i) {
+        const float a = normals[3 * i], b = normals[3 * i + 1], c = normals[3 * i + 2];
+        const float l2 = std::fma(c, c, std::fma(b, b, a * a));
+        if (!std::isfinite(l2) || !(l2 > 0.0f)) {
+            set_error("si_mesh_create: normal %lld is zero or not finite", (long long)i);
+            return SI_ERR_INVALID;
+        }
+    }
     cudaStream_t s = (cudaStream_t)stream;
     Mesh *m = new Mesh();
     SI_CUDA(cudaGetDevice(&m->device));
     m->n = n;
     const float *dp = points, *dn = normals;
     float *tmp_p = nullptr, *tmp_n = nullptr;
-    unsigned *scratch = nullptr;  // 6 bbox keys + 1 bad flag
-    unsigned host_scratch[7];
     si_status st = SI_OK;
     cudaError_t e = cudaSuccess;
     do {
         if ((st = dev_alloc((void **)&m->pos, sizeof(float4) * n, s)) != SI_OK) break;
         if ((st = dev_alloc((void **)&m->nrm, sizeof(float4) * n, s)) != SI_OK) break;
         if ((st = dev_alloc((void **)&m->flags, sizeof(unsigned), s)) != SI_OK) break;
+        if ((st = dev_alloc((void **)&m->bbox_keys, sizeof(unsigned) * 8, s)) != SI_OK) break;
         e = cudaEventCreateWithFlags(&m->ready, cudaEventDisableTiming);
         if (e != cudaSuccess) break;
         e = cudaMemsetAsync(m->flags, 0, sizeof(unsigned), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(m->bbox_keys, 0xff, sizeof(unsigned) * 3, s);  // min keys
+        if (e == cudaSuccess) e = cudaMemsetAsync(m->bbox_keys + 3, 0, sizeof(unsigned) * 5, s);  // max keys
         if (e != cudaSuccess) break;
-        if (!is_device_pointer(points)) {
+        if (!dev_p) {
             if ((st = dev_alloc((void **)&tmp_p, sizeof(float) * 3 * n, s)) != SI_OK) break;
             e = cudaMemcpyAsync(tmp_p, points, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s);
             if (e != cudaSuccess) break;
             dp = tmp_p;
         }
-        if (!is_device_pointer(normals)) {
+        if (!dev_n) {
             if ((st = dev_alloc((void **)&tmp_n, sizeof(float) * 3 * n, s)) != SI_OK) break;
             e = cudaMemcpyAsync(tmp_n, normals, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s);
             if (e != cudaSuccess) break;
             dn = tmp_n;
         }
-        if ((st = dev_alloc((void **)&scratch, sizeof(unsigned) * 8, s)) != SI_OK) break;
-        unsigned init[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 0u, 0u};
-        e = cudaMemcpyAsync(scratch, init, sizeof(init), cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) break;
-        mesh_ingest_kernel<<<grid_blocks(n), 256, 0, s>>>(dp, dn, n, m->pos, m->nrm, scratch, scratch + 6);
+        mesh_ingest_kernel<<<grid_blocks(n), 256, 0, s>>>(dp, dn, n, m->pos, m->nrm, m->bbox_keys, m->flags);
         note_launches(1);
         e = cudaGetLastError();
         if (e != cudaSuccess) break;
-        e = cudaMemcpyAsync(host_scratch, scratch, sizeof(host_scratch), cudaMemcpyDeviceToHost, s);
-        if (e != cudaSuccess) break;
         e = cudaEventRecord(m->ready, s);
-        if (e != cudaSuccess) break;
-        e = cudaStreamSynchronize(s);
     } while (0);
     if (tmp_p) dev_free(tmp_p, s);
     if (tmp_n) dev_free(tmp_n, s);
-    if (scratch) dev_free(scratch, s);
     if (e != cudaSuccess && st == SI_OK) st = cuda_fail(e, "si_mesh_create");
-    if (st == SI_OK && host_scratch[6] != 0) {
-        set_error("si_mesh_create: a coordinate is not finite or a normal has zero length");
-        st = SI_ERR_INVALID;
-    }
     if (st != SI_OK) {
         cudaStreamSynchronize(s);
         dev_free(m->pos, s);
         dev_free(m->nrm, s);
         dev_free(m->flags, s);
+        dev_free(m->bbox_keys, s);
         if (m->ready) cudaEventDestroy(m->ready);
+        cudaStreamSynchronize(s);
         delete m;
         return st;
     }
-    for (int k = 0; k < 3; ++k) {
-        unsigned klo = host_scratch[k], khi = host_scratch[3 + k];
-        unsigned blo = (klo & 0x80000000u) ? (klo & 0x7fffffffu) : ~klo;
-        unsigned bhi = (khi & 0x80000000u) ? (khi & 0x7fffffffu) : ~khi;
-        std::memcpy(&m->bmin[k], &blo, 4);
-        std::memcpy(&m->bmax[k], &bhi, 4);
-    }
     *out_mesh = reinterpret_cast<si_mesh_t>(m);
     return SI_OK;
+}
+}  // namespace si
+
+extern "C" {
+
+si_status si_mesh_create(const float *points, const float *normals, int64_t n, si_stream stream,
+                         si_mesh_t *out_mesh) {
+    return si::mesh_create(points, normals, n, stream, out_mesh, true);
 }
 
 si_status si_mesh_destroy(si_mesh_t mesh) {
@@ -360,6 +403,8 @@ si_status si_mesh_destroy(si_mesh_t mesh) {
     dev_free(m->pos, nullptr);
     dev_free(m->nrm, nullptr);
     dev_free(m->flags, nullptr);
+    dev_free(m->bbox_keys, nullptr);
+    cudaStreamSynchronize(nullptr);
     if (m->ready) cudaEventDestroy(m->ready);
     delete m;
     cudaSetDevice(prev);

@@ -184,12 +184,7 @@ extern "C" si_status si_generate_noalloc(si_mesh_t mesh, const int32_t *query_id
     d.query_idx = query_idx;
     d.out = out;
     d.flags = me->flags;
-    for (int a = 0; a < 3; ++a) {
-        d.origin[a] = g->origin[a];
-        d.dims[a] = g->dims[a];
-    }
-    d.cell = g->cell_len;
-    d.inv_cell = g->inv_cell;
+    d.geom = g->geom;
     d.m = m;
     d.n_points = (int)me->n;
     d.W = W;
@@ -209,9 +204,6 @@ extern "C" si_status si_generate_noalloc(si_mesh_t mesh, const int32_t *query_id
     d.invB = 1.0f / bin_size;
     d.halfW = 0.5f * (float)W;
     d.umax = (float)(W - 1);
-    float mag = 0.0f;
-    for (int a = 0; a < 3; ++a) mag = fmaxf(mag, fmaxf(fabsf(me->bmin[a]), fabsf(me->bmax[a])));
-    d.margin = (float)(1e-5 * ((double)mag + d.Rc + g->cell_len) + 1e-30);
 
     SI_CUDA(cudaStreamWaitEvent(st, g->ready, 0));
     noalloc_setup_kernel<<<1, 256, 0, st>>>(d, schedule.kind, (int)units, P, mc, (int)nsteps, scratch);

@@ -45,6 +45,20 @@ namespace si {
 
 namespace {
 
+// Index checks of the SI_DEBUG_BOUNDS build: a failed check sets the item's
+// kFlagBounds (si_get_stats reports it) and the access is skipped or pointed
+// at valid memory; nothing traps.  In the normal build the checks are `true`
+// and their conditions are not evaluated.
+#ifdef SI_DEBUG_BOUNDS
+__device__ __forceinline__ bool bounds_ok(bool c, unsigned *flags) {
+    if (!c) atomicOr(flags, kFlagBounds);
+    return c;
+}
+#define SI_IN_BOUNDS(cond, flags) bounds_ok((cond), (flags))
+#else
+#define SI_IN_BOUNDS(cond, flags) true
+#endif
+
 constexpr int kWarps = kThreads / 32;
 // Two ways to run the tile ring, chosen per group shape:
 //  * barrier mode (groups of 8+ images): every warp consumes; after each tile
@@ -77,6 +91,7 @@ struct __align__(16) Header {
     int slot_cnt[32];         // sliced groups: contributing pairs per image of this slice
     int cur_r, cur_o;          // barrier mode: producer row cursor
     unsigned long long t_step;  // heterogeneity emulation: start of a slow block's step
+    unsigned long long t_trace; // claim trace: start of the current claim's work
     // adaptive weighted factoring: this worker's claim and its measured rate
     int awf_lo, awf_hi;
     unsigned long long awf_t0;  // when the current chunk was claimed
@@ -157,9 +172,13 @@ __device__ int block_scan_rows(const int *len, int *off, int nr, Header &H) {
     return total;
 }
 
-// Constants of one item that the pair evaluation needs.
+// Constants of one item that the pair evaluation needs (and, for the
+// SI_DEBUG_BOUNDS build, the group's image words and the item's flags).
 struct PairConsts {
     float Rc2, cosS, invB, halfW, umax, B;
+    const int *img;
+    int img_words;
+    unsigned *flags;
 };
 
 // Shape of a group's images: compile-time when WT > 0, else runtime.
@@ -242,6 +261,7 @@ __device__ __forceinline__ void eval_pair(const PairDist &pd, const float4 NX, c
     if (in) {
         const int rw = sh.row_words(), S = sh.S();
         int *p0 = img_adj + ((int)(Ub >> 16) * rw + (int)(Vb >> 16) * S);
+        if (!SI_IN_BOUNDS(p0 >= k.img && p0 + rw + S < k.img + k.img_words, k.flags)) return;
         const uint32_t w01 = Bq - w11;
         atomicAdd(p0, (int)(65536u - A - w01));  // w00 = 2^16 - A - Bq + w11
         atomicAdd(p0 + rw, (int)(A - w11));
@@ -275,7 +295,9 @@ __device__ __forceinline__ void eval_pair_nearest(const PairDist &pd, const floa
         if (live & (ca >= k.cosS)) atomicAdd(pc_s + 96, 1);  // live is the cull here: angle-passing candidates
     }
     if (in) {
-        atomicAdd(img_q + (int)kr * sh.row_words() + ((int)lc << sh.log2S()), 1);
+        int *p = img_q + (int)kr * sh.row_words() + ((int)lc << sh.log2S());
+        if (!SI_IN_BOUNDS(p >= k.img && p < k.img + k.img_words, k.flags)) return;
+        atomicAdd(p, 1);
         ++cnt;
     }
 }
@@ -416,11 +438,14 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
     const int64_t m = it.m;
     const float4 *__restrict__ pn = it.pn;
     const int *__restrict__ cstart = it.cell_start;
-    const float ox = it.origin[0], oy = it.origin[1], oz = it.origin[2];
-    const float cell = it.cell, inv = it.inv_cell, margin = it.margin;
-    const int dx_ = it.dims[0], dy_ = it.dims[1], dz_ = it.dims[2];
-    const PairConsts k{it.Rc2, it.cosS, it.invB, it.halfW, it.umax, it.B};
+    const GridGeom &gg = *it.geom;
+    const float ox = gg.origin[0], oy = gg.origin[1], oz = gg.origin[2];
+    const float cell = gg.cell_len, inv = gg.inv_cell;
+    const int dx_ = gg.dims[0], dy_ = gg.dims[1], dz_ = gg.dims[2];
+    PairConsts k{it.Rc2, it.cosS, it.invB, it.halfW, it.umax, it.B, nullptr, 0, it.flags};
     const float Rc = it.Rc;
+    // stencil safety margin: a few ulps of the coordinates and of the radius
+    const float margin = 1e-5f * (gg.mag + Rc + gg.cell_len) + 1e-30f;
     const int slot = lane & (S - 1);
     // candidates per tile: a compile-time constant for the specialised shapes
     constexpr int TNC = WT > 0 ? tile_for_shape(WT, LS) : 0;
@@ -432,6 +457,8 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
         return true;
     }
     const int img_words_pad = ((S * W1 * W1) + 3) & ~3;
+    k.img = img;
+    k.img_words = img_words_pad;
 
     // unit u = slice `sl` of group `g`: with K slices per group, K blocks share
     // the group's candidate stream and add their partial images into `out`
@@ -454,6 +481,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
                 sp = ok ? it.sorted_pos[src] : 0;
             }
             if (!ok) atomicOr(it.flags, kFlagBadQuery);
+            if (!SI_IN_BOUNDS((unsigned)sp < (unsigned)it.n_points, it.flags)) sp = 0;
             Q[tid].p = pn[2 * (int64_t)sp];
             Q[tid].n = pn[2 * (int64_t)sp + 1];
             Q[tid].slot = ok ? q : -1;
@@ -536,8 +564,10 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
                 const int x0 = cell_coord(H.gmin[0] - rx, ox, inv, dx_);
                 const int x1 = cell_coord(H.gmax[0] + rx, ox, inv, dx_);
                 const int c0 = (z * dy_ + y) * dx_ + x0;
-                start = cstart[c0];
-                len = cstart[c0 + (x1 - x0) + 1] - start;
+                if (SI_IN_BOUNDS(c0 >= 0 && x1 >= x0 && c0 + (x1 - x0) + 1 <= gg.ncell, it.flags)) {
+                    start = cstart[c0];
+                    len = cstart[c0 + (x1 - x0) + 1] - start;
+                }
             }
             sv.row_start[r] = start;
             sv.row_len[r] = len;
@@ -584,8 +614,10 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
                             continue;
                         }
                         const int take = min(need - done, avail);
-                        bulk_copy_g2s(dst + 2 * done, pn + 2 * (int64_t)(sv.row_start[cr] + co),
-                                      (uint32_t)take * 32u, &H.bar[b]);
+                        int src0 = sv.row_start[cr] + co;
+                        if (!SI_IN_BOUNDS(done + take <= TN && src0 >= 0 && src0 + take <= it.n_points, it.flags))
+                            src0 = 0;  // keep the copy (its bytes complete the stage) inside the mesh
+                        bulk_copy_g2s(dst + 2 * done, pn + 2 * (int64_t)src0, (uint32_t)take * 32u, &H.bar[b]);
                         done += take;
                         co += take;
                     }
@@ -651,8 +683,10 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
                     continue;
                 }
                 const int take = min(need - done, avail);
-                bulk_copy_g2s(dst + 2 * done, pn + 2 * (int64_t)(sv.row_start[cr] + co), (uint32_t)take * 32u,
-                              &H.bar[b]);
+                int src0 = sv.row_start[cr] + co;
+                if (!SI_IN_BOUNDS(done + take <= TN && src0 >= 0 && src0 + take <= it.n_points, it.flags))
+                    src0 = 0;  // keep the copy (its bytes complete the stage) inside the mesh
+                bulk_copy_g2s(dst + 2 * done, pn + 2 * (int64_t)src0, (uint32_t)take * 32u, &H.bar[b]);
                 done += take;
                 co += take;
             }
@@ -725,7 +759,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
             const int q = (c << lv) + k;
             if (k >= (1 << lv) || q >= nq) continue;
             const int qs = Q[q].slot;
-            if (qs >= 0) {
+            if (qs >= 0 && SI_IN_BOUNDS(qs < m && p < npix, it.flags)) {
                 if (K == 1)
                     __stcs(out + (int64_t)qs * npix + p, v[k]);
                 else if (v[k] != 0)
@@ -933,6 +967,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks_for<MODES>()) spin_kernel
                 H.claim = s;
             }
             if ((int)blockIdx.x < a.slow_workers) H.t_step = global_ns();
+            if (a.trace) H.t_trace = global_ns();
         }
         __syncthreads();
         const int step = H.claim;
@@ -983,6 +1018,18 @@ __global__ void __launch_bounds__(kThreads, min_blocks_for<MODES>()) spin_kernel
             if (idle > kSlowIdleCapNs) idle = kSlowIdleCapNs;
             const uint64_t until = global_ns() + idle;
             while (global_ns() < until) __nanosleep(2000);
+        }
+        if (a.trace && tid == 0 && alive) {
+            // the claim's entry: worker, step, start and end of its work (a slow
+            // worker's idle included: it stands for the slower processor)
+            const unsigned long long e = atomicAdd(a.trace_count, 1ull);
+            if ((int64_t)e < a.trace_cap) {
+                int64_t *t = a.trace + 4 * (int64_t)e;
+                t[0] = blockIdx.x;
+                t[1] = step;
+                t[2] = (int64_t)H.t_trace;
+                t[3] = (int64_t)global_ns();
+            }
         }
     }
     // ---- the last block to finish resets the dynamic step counter for the next launch

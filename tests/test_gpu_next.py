@@ -197,3 +197,42 @@ def test_awf_balances_slow_workers():
         assert awf <= 1.3 * fac, (awf, fac)
     finally:
         spin.si_mesh_destroy(mesh)
+
+
+@pytest.mark.parametrize("kind", ["STATIC", "SS", "GSS", "FAC"])
+def test_claim_trace_covers_every_step_once(kind):
+    """si_generate_traced records one entry per scheduling claim: each step of
+    the rule's chunk table exactly once (STATIC: one per worker), start before
+    end, and the images are those of si_generate."""
+    import torch
+
+    import paper_1811_00901_gb300 as spin
+    dev = torch.device("cuda:0")
+    pts, nrm = wl.heightfield(20000, 51)
+    W, B, c = 32, 0.01, float(wl.cos_deg(60.0))
+    m = pts.shape[0]
+    sched = spin.make_schedule(kind, group=16, slices=1)
+    P = spin.si_default_workers(W, sched)
+    mesh = spin.si_mesh_create(torch.from_numpy(pts).to(dev), torch.from_numpy(nrm).to(dev))
+    try:
+        ref = torch.empty((m, W, W), dtype=torch.int32, device=dev)
+        spin.si_generate(mesh, None, m, W, B, c, sched, ref)
+        out = torch.empty_like(ref)
+        claims = torch.full((4 * P + 4096, 4), -1, dtype=torch.int64, device=dev)
+        count = torch.zeros(1, dtype=torch.int64, device=dev)
+        spin.si_generate_traced(mesh, None, m, W, B, c, sched, out, claims, count)
+        torch.cuda.synchronize()
+        spin.si_get_stats(mesh)
+    finally:
+        spin.si_mesh_destroy(mesh)
+    assert torch.equal(out, ref)
+    n = int(count.item())
+    tr = claims[:n].cpu().numpy()
+    units = (m + 15) // 16
+    steps = len(spin.si_chunk_table(kind, units, P, 1)) - 1
+    assert n == steps
+    assert sorted(tr[:, 1].tolist()) == list(range(steps))
+    assert np.all(tr[:, 2] <= tr[:, 3]) and np.all(tr[:, 0] >= 0) and np.all(tr[:, 0] < P)
+    if kind == "STATIC":
+        np.testing.assert_array_equal(np.sort(tr[:, 0]), np.arange(P))
+        np.testing.assert_array_equal(tr[:, 0], tr[:, 1])  # worker k runs block k

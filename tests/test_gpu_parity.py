@@ -248,12 +248,33 @@ def test_invalid_arguments_are_rejected():
         spin.si_mesh_destroy(mesh)
     bad_n = nrm.copy()
     bad_n[5] = 0
-    with pytest.raises(spin.SpinError):
-        spin.si_mesh_create(torch.from_numpy(pts).to(dev), torch.from_numpy(bad_n).to(dev))
     bad_p = pts.copy()
     bad_p[7, 1] = np.nan
-    with pytest.raises(spin.SpinError):
-        spin.si_mesh_create(torch.from_numpy(bad_p).to(dev), torch.from_numpy(nrm).to(dev))
+    # host inputs: rejected by si_mesh_create itself
+    for p_, n_ in ((pts, bad_n), (bad_p, nrm)):
+        with pytest.raises(spin.SpinError) as e:
+            spin.si_mesh_create(torch.from_numpy(p_), torch.from_numpy(n_))
+        assert e.value.status == spin.SI_ERR_INVALID
+    # device inputs: checked on the device without a round trip, reported by si_get_stats
+    for p_, n_ in ((pts, bad_n), (bad_p, nrm)):
+        mesh = spin.si_mesh_create(torch.from_numpy(p_).to(dev), torch.from_numpy(n_).to(dev))
+        try:
+            spin.si_generate(mesh, None, 100, 16, 0.05, 0.5, spin.make_schedule("GSS"), out)
+            st, status = spin.si_get_stats(mesh, raise_on_flags=False)
+            assert status == spin.SI_ERR_INVALID and st["bad_input"] == 1
+        finally:
+            spin.si_mesh_destroy(mesh)
+    # the host-buffer entry point checks on the device and reports before it returns
+    hout = torch.empty((100, 16, 16), dtype=torch.int32)
+    with pytest.raises(spin.SpinError) as e:
+        spin.si_generate_host(torch.from_numpy(pts), torch.from_numpy(bad_n), 100, None, 100, 16, 0.05, 0.5,
+                              spin.make_schedule("GSS"), hout)
+    assert e.value.status == spin.SI_ERR_INVALID
+    # a clean mesh reports nothing
+    mesh = spin.si_mesh_create(torch.from_numpy(pts).to(dev), torch.from_numpy(nrm).to(dev))
+    st, status = spin.si_get_stats(mesh, raise_on_flags=False)
+    assert status == spin.SI_OK and st["bad_input"] == 0
+    spin.si_mesh_destroy(mesh)
 
 
 def test_overflow_is_detected():
