@@ -82,15 +82,17 @@ typedef enum si_sched_kind {
                              x_j = 2 + b_j^2 + b_j sqrt(b_j^2 + 4) (j >= 1), cov = sigma / mu of the
                              iteration time (si_schedule.fac_cov), evaluated in IEEE double;
                              >= min_chunk */,
-    SI_SCHED_AWF = 5      /* adaptive weighted factoring: batches of P chunks as FAC (the FAC2 chunk
-                             of each batch, computed for the call's whole loop), each chunk scaled by
-                             the requesting worker's weight w = rate / (mean rate of the workers
-                             measured so far), rate = its groups done / its time so far (measured on
-                             the device, updated after every chunk; w = 1 before a worker's first
-                             chunk ends; w clamped to [0.05, 20]); chunk = max(min_chunk,
-                             round(w x batch chunk)).  Chunk sizes depend on measured times and are
-                             decided on the device; every group is still generated exactly once.
-                             In a batched call every item must use it. */
+    SI_SCHED_AWF = 5      /* adaptive weighted factoring: batches of P chunks as FAC, the batch
+                             chunk being FAC2 on the groups that remain at the claim, ceil(R / (2P)),
+                             and half that for the first batch (claims 0 .. P-1, made before any
+                             rate exists); each chunk scaled by the requesting worker's weight
+                             w = rate / (mean rate of the workers measured so far), rate = its groups
+                             done / its time so far (measured on the device, updated after every
+                             chunk; w = 1 before a worker's first chunk ends; w clamped to
+                             [0.05, 20]); chunk = max(min_chunk, round(w x batch chunk)).  Chunk
+                             sizes depend on measured times and are decided on the device; every
+                             group is still generated exactly once.  In a batched call every item
+                             must use it. */
 } si_sched_kind;
 
 /* How a contributing pair is counted into its image. */

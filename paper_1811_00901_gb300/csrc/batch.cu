@@ -123,7 +123,7 @@ struct Plan {
     // adaptive weighted factoring: unit bases of the items and FAC2 batch chunks
     bool awf = false;
     int awf_min_chunk = 1;
-    std::vector<int> awf_ubase, awf_batch;
+    std::vector<int> awf_ubase;
     bool all_static = true;
     int nsteps = 0;
     std::vector<Piece> pieces;
@@ -139,7 +139,7 @@ struct Plan {
     std::vector<int64_t> split_base, counts_off;
     int64_t split_images = 0;
     size_t o_ctr = 0, o_items = 0, o_pieces = 0, o_steps = 0, o_sitems = 0, o_sqbase = 0, o_split = 0,
-           o_split_items = 0, o_awf_ubase = 0, o_awf_batch = 0, o_hist = 0, o_perm = 0, o_counts = 0,
+           o_split_items = 0, o_awf_ubase = 0, o_hist = 0, o_perm = 0, o_counts = 0,
            total_bytes = 0;
     bool empty = false;
 };
@@ -257,9 +257,6 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
                 break;
             }
         p->awf_min_chunk = mc;
-        std::vector<int64_t> st;
-        chunk_table(SI_SCHED_FAC, total_units, workers, mc, 0.0, &st);
-        for (size_t s = 0; s + 1 < st.size(); s += (size_t)workers) p->awf_batch.push_back((int)(st[s + 1] - st[s]));
         p->nsteps = 0;
     } else if (p->all_static) {
         // PSIA: block b gets the contiguous block [floor(bU/P), floor((b+1)U/P)) of
@@ -336,8 +333,7 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
     p->o_split = align_up(p->o_sqbase + sizeof(int64_t) * p->sqbase.size(), 256);
     p->o_split_items = align_up(p->o_split + sizeof(int64_t) * p->split_base.size(), 256);
     p->o_awf_ubase = align_up(p->o_split_items + sizeof(int) * p->split_items.size(), 256);
-    p->o_awf_batch = align_up(p->o_awf_ubase + sizeof(int) * p->awf_ubase.size(), 256);
-    p->o_hist = align_up(p->o_awf_batch + sizeof(int) * p->awf_batch.size(), 256);
+    p->o_hist = align_up(p->o_awf_ubase + sizeof(int) * p->awf_ubase.size(), 256);
     p->o_perm = align_up(p->o_hist + sizeof(int) * (p->htot + 1), 256);
     p->o_counts = align_up(p->o_perm + sizeof(int) * p->qtot, 256);
     p->total_bytes = align_up(p->o_counts + sizeof(int) * p->split_images, 256);
@@ -413,7 +409,6 @@ void fill_blob(const Plan &p, const std::vector<si_batch_item> &items, const std
     }
     if (p.awf) {
         std::memcpy(h + (p.o_awf_ubase - p.o_items), p.awf_ubase.data(), sizeof(int) * p.awf_ubase.size());
-        std::memcpy(h + (p.o_awf_batch - p.o_items), p.awf_batch.data(), sizeof(int) * p.awf_batch.size());
     }
 }
 
@@ -471,8 +466,6 @@ si_status record_batch(const Plan &p, const std::vector<si_batch_item> &items, c
         a.awf = 1;
         a.total_units = p.awf_ubase.back();
         a.unit_base = reinterpret_cast<const int *>(scratch + p.o_awf_ubase);
-        a.awf_batch = reinterpret_cast<const int *>(scratch + p.o_awf_batch);
-        a.awf_nbatch = (int)p.awf_batch.size();
         a.min_chunk = p.awf_min_chunk;
     }
     // heterogeneity emulation: at most every launched block is slow

@@ -176,8 +176,6 @@ struct LaunchArgs {
     int awf = 0;
     int total_units = 0;             // units of all items
     const int *unit_base = nullptr;  // [nitems + 1]: first unit of each item in the concatenation
-    const int *awf_batch = nullptr;  // FAC2 chunk of batch j, j < awf_nbatch
-    int awf_nbatch = 0;
     int min_chunk = 1;
     // claim trace (si_generate_traced): [trace_cap][4] worker, step, start, end
     int64_t *trace = nullptr;

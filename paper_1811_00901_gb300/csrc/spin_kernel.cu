@@ -41,6 +41,7 @@
 #include "device_common.cuh"
 #include "internal.h"
 
+
 namespace si {
 
 namespace {
@@ -807,9 +808,9 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
 
 // Adaptive weighted factoring, the request half of getChunk run on the device
 // by thread 0 of a worker: fold the chunk just finished into the worker's
-// rate, take the next claim's FAC2 batch chunk, scale it by the worker's
-// weight (its rate over the mean of the measured rates) and take that many
-// units from the shared cursor.  Sets H.claim (the claim index), H.awf_lo and
+// rate, take the batch chunk (FAC2 on the units that remain, the first batch
+// at half size), scale it by the worker's weight (its rate over the mean of
+// the measured rates) and take that many units from the shared cursor.  Sets H.claim (the claim index), H.awf_lo and
 // H.awf_hi.
 __device__ void awf_claim(const LaunchArgs &a, Header &H, const int claim_iter, const bool first_slow) {
     const uint64_t now = global_ns();
@@ -826,7 +827,13 @@ __device__ void awf_claim(const LaunchArgs &a, Header &H, const int claim_iter, 
         first_slow ? (unsigned long long)blockIdx.x
                    : (unsigned long long)a.slow_workers + atomicAdd(&a.ctr->awf_claims, 1ull);
     const unsigned long long j = s / gridDim.x;
-    const int batch = j < (unsigned long long)a.awf_nbatch ? a.awf_batch[j] : a.min_chunk;
+    // the batch chunk: FAC2 on what remains now, ceil(R / (2P)); the first batch
+    // (claims 0 .. P-1, made before any rate exists) at half that, so a slow
+    // worker's first chunk cannot set the makespan on its own
+    const unsigned long long cur = *(volatile unsigned long long *)&a.ctr->awf_next;
+    const long long rem = cur >= (unsigned long long)a.total_units ? 0 : (long long)a.total_units - (long long)cur;
+    const long long div = 2ll * gridDim.x * (j == 0 ? 2 : 1);
+    const int batch = (int)max((long long)a.min_chunk, (rem + div - 1) / div);
     double w = 1.0;
     const unsigned rated = *(volatile unsigned *)&a.ctr->awf_rated;
     const double sum = *(volatile double *)&a.ctr->awf_rate_sum;

@@ -162,11 +162,12 @@ def test_awf_batched_items_share_one_loop():
 
 
 def test_awf_balances_slow_workers():
-    """With half the workers 4x slower, AWF moves work to the fast workers: it
-    finishes well before STATIC (which waits for the slow workers' equal
-    blocks) and close to FAC.  Both start with FAC2's first batch, which at a
-    4x slowdown already sets the makespan near half of STATIC's once chunks
-    are fine (here about 25 groups per worker)."""
+    """With half the workers 4x slower (and requesting first), AWF moves work
+    to the fast workers: it finishes well before STATIC (which waits for the
+    slow workers' equal blocks) and before FAC, whose first batch of FAC2
+    chunks is what sets its makespan at this slowdown (AWF's first batch is
+    half as large and its later chunks follow the measured rates).  About 25
+    groups per worker."""
     import torch
 
     import paper_1811_00901_gb300 as spin
@@ -194,7 +195,7 @@ def test_awf_balances_slow_workers():
         fac = kernel_ms(spin.make_schedule("FAC", num_workers=P, group=8, slow_workers=P // 2, slowdown=4.0))
         awf = kernel_ms(spin.make_schedule("AWF", num_workers=P, group=8, slow_workers=P // 2, slowdown=4.0))
         assert awf <= 0.7 * static, (awf, static)
-        assert awf <= 1.3 * fac, (awf, fac)
+        assert awf < fac, (awf, fac)
     finally:
         spin.si_mesh_destroy(mesh)
 
