@@ -99,8 +99,8 @@ si_status match_tc(const int32_t *scene, int64_t n_scene, const int32_t *model, 
     unsigned *err = nullptr;
     si_status s = dev_alloc((void **)&a, sizeof(__nv_bfloat16) * (size_t)n_scene * kk, st);
     if (s == SI_OK) s = dev_alloc((void **)&b, sizeof(__nv_bfloat16) * (size_t)n_model * kk, st);
-    if (s == SI_OK) s = dev_alloc((void **)&pv, sizeof(float) * (size_t)parts * n_scene * k, st);
-    if (s == SI_OK) s = dev_alloc((void **)&pi, sizeof(int) * (size_t)parts * n_scene * k, st);
+    if (s == SI_OK) s = dev_alloc((void **)&pv, sizeof(float) * (size_t)2 * parts * n_scene * k, st);
+    if (s == SI_OK) s = dev_alloc((void **)&pi, sizeof(int) * (size_t)2 * parts * n_scene * k, st);
     if (s == SI_OK) s = dev_alloc((void **)&err, sizeof(unsigned), st);
     cudaError_t e = cudaSuccess;
     if (s == SI_OK) {

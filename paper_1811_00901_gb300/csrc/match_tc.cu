@@ -15,12 +15,15 @@
 //     memory descriptors, FP32 accumulation in TMEM); tcgen05.commit releases a
 //     ring stage when the MMAs reading it are done, and hands a finished
 //     accumulator to the epilogue;
-//   * warps 2-5 read the accumulator out of TMEM (tcgen05.ld, lane i = scene
-//     row i of the block, one thread per row) and offer every value to the
-//     row's running list of the k best (higher value first; model indices
-//     arrive in increasing order, so equal values keep the smaller index);
-//     the second accumulator lets the next tile's MMAs run meanwhile.
-// Each CTA writes its rows' lists; merge_parts_kernel combines the parts.
+//   * warps 2-9 read the accumulator out of TMEM (tcgen05.ld, lane i = scene
+//     row i of the block): two threads per row, one for each half of the
+//     tile's columns, each loading its whole share into registers before it
+//     hands the buffer back, so the next tile's MMAs overlap the scan; each
+//     thread keeps a running list of its row's k best in registers (higher
+//     value first; model indices arrive in increasing order, so equal values
+//     keep the smaller index).
+// Each CTA writes two lists per row (one per column half);
+// merge_parts_kernel combines the lists of all parts.
 //
 // Every mbarrier wait is bounded (kWaitLimitNs of %globaltimer): on expiry the
 // CTA sets the error word, stops issuing, waits (bounded) for the copies and
@@ -47,7 +50,8 @@ constexpr int kAStageBytes = kBM * kBK * 2;   // 16 KB
 constexpr int kBStageBytes = kBN * kBK * 2;   // 32 KB
 constexpr int kStageBytes = kAStageBytes + kBStageBytes;
 constexpr int kTmemCols = 2 * kBN;   // two FP32 accumulators of 128 lanes x 256 columns
-constexpr int kTcThreads = 192;      // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kEpiWarps = 8;         // two per TMEM lane quarter, each scanning half of a tile's columns
+constexpr int kTcThreads = 32 * (2 + kEpiWarps);  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int kTcSmem = 1024 + kStagesTc * kStageBytes + 256;
 
 struct TcBarriers {
@@ -86,9 +90,9 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t
         : "memory");
 }
 
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+// Issues a load of 32 consecutive FP32 columns of this thread's TMEM lane;
+// the registers hold them after tc_wait_ld().
+__device__ __forceinline__ void tc_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
         "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -97,9 +101,15 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
           "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
           "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Ties the registers of an issued TMEM load to this point of the program, so
+// that no use of them is scheduled above the preceding tc_wait_ld().
+__device__ __forceinline__ void tc_pin(uint32_t (&r)[32]) {
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 32; ++i) asm volatile("" : "+r"(r[i]));
 }
 
 // Shared-memory matrix descriptor of a K-major BF16 tile written by TMA with
@@ -133,20 +143,49 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile
     return false;
 }
 
-// Inserts (x, j) into a descending list of k (strictly better than its k-th,
-// which the caller checked); returns the new k-th value.
-__device__ __noinline__ float topk_push(float *v, int *ix, int k, float x, int j) {
-    int q = k - 1;
-    while (q > 0 && v[q - 1] < x) {
-        v[q] = v[q - 1];
-        ix[q] = ix[q - 1];
-        --q;
-    }
-    v[q] = x;
-    ix[q] = j;
-    return v[k - 1];
+// The largest of 32 values by a balanced tree.
+__device__ __forceinline__ float chunk_max(const float (&x)[32]) {
+    float m[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) m[u] = fmaxf(x[u], x[u + 16]);
+#pragma unroll
+    for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+        for (int u = 0; u < w; ++u) m[u] = fmaxf(m[u], m[u + w]);
+    return m[0];
 }
 
+// Inserts (x, j) into a descending list held in the first k of L register
+// slots (x strictly better than the k-th, which the caller checked): one pass
+// in which every index is compile-time, so the list stays in registers.  From
+// the first slot x beats on, the entries shift down one place; an equal value
+// stays ahead of x (x comes from a later column).  Returns the new k-th value.
+template <int L>
+__device__ __forceinline__ float topk_push(float (&v)[L], int (&ix)[L], int k, float x, int j) {
+    float cv = x;
+    int ci = j;
+    bool moving = false;
+    float kth = v[0];
+#pragma unroll
+    for (int q = 0; q < L; ++q) {
+        moving = moving || cv > v[q];
+        const bool sw = moving && q < k;
+        const float tv = v[q];
+        const int ti = ix[q];
+        v[q] = sw ? cv : tv;
+        ix[q] = sw ? ci : ti;
+        cv = sw ? tv : cv;
+        ci = sw ? ti : ci;
+        if (q == k - 1) kth = v[q];
+    }
+    return kth;
+}
+
+// L = register slots of each thread's list (k <= L).  A block of ten warps
+// gets at most 168 registers a thread (three of its warps share one
+// sub-partition's 16K registers), which a tile share of 128 values and a
+// 16-slot list overflow; k <= 8 runs with 8 slots.
+template <int L>
 __global__ void __launch_bounds__(kTcThreads, 1)
     match_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                     const int n_scene, const int n_model, const int k_slices, const int tiles, const int parts,
@@ -172,7 +211,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&B.tfull[b], 1);
-            mbar_init(&B.tempty[b], 4);
+            mbar_init(&B.tempty[b], kEpiWarps);
         }
         mbar_init(&B.drain, 1);
         B.abort = 0;
@@ -248,12 +287,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_wait_bounded(&B.drain, 0u, kWaitLimitNs);
         }
     } else {
-        // ---- epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31, one scene row per thread
+        // ---- epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31, one scene row per
+        // thread; warps 2-5 take the first half of each tile's columns, 6-9 the second
         const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int row = quarter * 32 + lane;
-        float v[kMatchTcMaxK];
-        int ix[kMatchTcMaxK];
-        for (int q = 0; q < kMatchTcMaxK; ++q) {
+        constexpr int kChunks = kBN / 32 / 2;  // 32-column chunks per half tile
+        float v[L];
+        int ix[L];
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
             v[q] = -FLT_MAX;
             ix[q] = INT_MAX;
         }
@@ -263,36 +306,50 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const uint32_t tph = (uint32_t)(t >> 1) & 1u;
             if (!tc_wait(&B.tfull[b], tph, abort_flag)) break;
             tc_fence_after();
-            const int ncol0 = (t0 + t) * kBN;
-            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kBN);
-            for (int c = 0; c < kBN / 32; ++c) {
+            const int ncol0 = (t0 + t) * kBN + half * (kBN / 2);
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kBN + half * (kBN / 2));
+            // the warp's whole share of the tile into registers with one wait, then
+            // the buffer goes back to the MMA warp before any scanning
+            uint32_t r[kChunks][32];
+#pragma unroll
+            for (int c = 0; c < kChunks; ++c) tc_ld32_issue(taddr + (uint32_t)(c * 32), r[c]);
+            tc_wait_ld();
+#pragma unroll
+            for (int c = 0; c < kChunks; ++c) tc_pin(r[c]);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&B.tempty[b]);
+#pragma unroll
+            for (int c = 0; c < kChunks; ++c) {
                 float x[32];
-                tc_ld32(taddr + (uint32_t)(c * 32), x);
-                if (c == kBN / 32 - 1) {
-                    // all of this buffer is in registers: hand it back to the MMA warp
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&B.tempty[b]);
-                }
                 const int j0 = ncol0 + c * 32;
                 const int valid = n_model - j0;  // columns past the last model image hold zeros
-                if (valid >= 32) {
 #pragma unroll
-                    for (int u = 0; u < 32; ++u)
-                        if (x[u] > thr) thr = topk_push(v, ix, k, x[u], j0 + u);
-                } else {
-                    for (int u = 0; u < valid; ++u)
-                        if (x[u] > thr) thr = topk_push(v, ix, k, x[u], j0 + u);
+                for (int u = 0; u < 32; ++u) x[u] = u < valid ? __uint_as_float(r[c][u]) : -FLT_MAX;
+                // the list changes only where the chunk's maximum beats its k-th value; then
+                // the maximum (the smallest column among equals) goes in and leaves the
+                // chunk, and the next maximum is tried: one insertion site keeps the code small
+                float mx = chunk_max(x);
+                while (mx > thr) {
+                    int pos = 31;
+#pragma unroll
+                    for (int u = 31; u >= 0; --u) pos = x[u] == mx ? u : pos;
+                    thr = topk_push(v, ix, k, mx, j0 + pos);
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) x[u] = u == pos ? -FLT_MAX : x[u];
+                    mx = chunk_max(x);
                 }
             }
         }
         const int grow = mb * kBM + row;
         if (grow < n_scene && !*abort_flag) {
-            const int64_t o = ((int64_t)part * n_scene + grow) * k;
-            for (int q = 0; q < k; ++q) {
-                part_v[o + q] = v[q];
-                part_i[o + q] = ix[q];
-            }
+            const int64_t o = ((int64_t)(2 * part + half) * n_scene + grow) * k;
+#pragma unroll
+            for (int q = 0; q < L; ++q)
+                if (q < k) {
+                    part_v[o + q] = v[q];
+                    part_i[o + q] = ix[q];
+                }
         }
     }
     tc_fence_before();
@@ -309,7 +366,7 @@ __device__ __forceinline__ bool better_vi(float va, int ia, float vb, int ib) {
     return va > vb || (va == vb && ia < ib);
 }
 
-// One thread per scene row: the k best of the parts' sorted lists.
+// One thread per scene row: the k best of the `parts` sorted lists.
 __global__ void merge_parts_kernel(const float *__restrict__ part_v, const int *__restrict__ part_i, int n_scene,
                                    int parts, int k, const unsigned *err, int32_t *__restrict__ best_idx,
                                    float *__restrict__ best_val) {
@@ -322,7 +379,7 @@ __global__ void merge_parts_kernel(const float *__restrict__ part_v, const int *
         }
         return;
     }
-    int head[kMatchTcMaxParts];
+    int head[2 * kMatchTcMaxParts];
     for (int p = 0; p < parts; ++p) head[p] = 0;
     for (int q = 0; q < k; ++q) {
         int bp = -1;
@@ -430,18 +487,22 @@ si_status match_tc_launch(const __nv_bfloat16 *a, int64_t n_scene, const __nv_bf
     {
         std::lock_guard<std::mutex> lk(attr_mu);
         if (dev >= 0 && dev < 128 && !attr_done[dev]) {
-            SI_CUDA(cudaFuncSetAttribute(match_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+            SI_CUDA(cudaFuncSetAttribute(match_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+            SI_CUDA(cudaFuncSetAttribute(match_tc_kernel<kMatchTcMaxK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kTcSmem));
             attr_done[dev] = true;
         }
     }
     const int64_t mblocks = (n_scene + kBM - 1) / kBM;
     const int tiles = (int)((n_model + kBN - 1) / kBN);
-    match_tc_kernel<<<(unsigned)(mblocks * parts), kTcThreads, kTcSmem, st>>>(
-        ma, mbm, (int)n_scene, (int)n_model, kp / kBK, tiles, parts, k, part_v, part_i, err);
+    auto kern = k <= 8 ? match_tc_kernel<8> : match_tc_kernel<kMatchTcMaxK>;
+    kern<<<(unsigned)(mblocks * parts), kTcThreads, kTcSmem, st>>>(ma, mbm, (int)n_scene, (int)n_model, kp / kBK,
+                                                                  tiles, parts, k, part_v, part_i, err);
     note_launches(1);
     SI_CUDA(cudaGetLastError());
-    merge_parts_kernel<<<(unsigned)((n_scene + 255) / 256), 256, 0, st>>>(part_v, part_i, (int)n_scene, parts, k,
-                                                                          err, best_idx, best_val);
+    // two lists per row and part: one per column half of the tiles
+    merge_parts_kernel<<<(unsigned)((n_scene + 255) / 256), 256, 0, st>>>(part_v, part_i, (int)n_scene, 2 * parts,
+                                                                          k, err, best_idx, best_val);
     note_launches(1);
     SI_CUDA(cudaGetLastError());
     return SI_OK;

@@ -19,7 +19,7 @@ constexpr int kMatchTcMaxParts = 32;   // model ranges per scene block, at most
 int match_tc_parts(int64_t n_scene, int64_t n_model, int sms);
 
 // a: [n_scene][kp], b: [n_model][kp] (BF16, rows 16-byte aligned, kp % 64 == 0);
-// part_v / part_i: [parts][n_scene][k] scratch; err: a zeroed device word.
+// part_v / part_i: [2 parts][n_scene][k] scratch; err: a zeroed device word.
 // Writes best_idx / best_val [n_scene][k]; if a bounded device wait gave up,
 // every best_idx of the call is -2.
 si_status match_tc_launch(const __nv_bfloat16 *a, int64_t n_scene, const __nv_bfloat16 *b, int64_t n_model, int kp,

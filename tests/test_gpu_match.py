@@ -117,7 +117,9 @@ def _run_bf16(scene, model, W, k, precision="BF16"):
 
 @pytest.mark.parametrize("W,k,n_scene,n_model,precision", [(16, 16, 257, 1025, "BF16"), (32, 5, 200, 3000, "BF16"),
                                                            (64, 3, 129, 600, "BF16"), (32, 7, 1000, 20000, "BF16"),
-                                                           (32, 5, 300, 2000, "FP32"), (16, 3, 130, 700, "FP32")])
+                                                           (32, 5, 300, 2000, "FP32"), (16, 3, 130, 700, "FP32"),
+                                                           # both list lengths of the kernel (8 and 16 slots) at their edge
+                                                           (32, 8, 300, 5000, "BF16"), (16, 9, 257, 1500, "FP32")])
 def test_tensor_core_exact_products_and_ties(W, k, n_scene, n_model, precision):
     """BF16 matching on the tensor cores with operands that BF16 holds exactly
     (balanced two-level images): every reported value equals the FP64
