@@ -589,9 +589,10 @@ def bench_trace(spin, torch, dev, c, shape, stream, het=None):
             "note": "imbalance = (latest - mean finishing time) / latest finishing time of the workers"}
 
 
-def bench_matching(spin, torch, dev, c, steps, warmup, stream, n_scene=16384, k=5):
-    """Spin-image matching: n_scene images of a rigidly moved copy of the bench
-    mesh against all images of the mesh (correlation over all bins, k best)."""
+def _matching_inputs(spin, torch, dev, c, n_scene, stream):
+    """The matching workload: every image of the bench mesh (the model) and
+    n_scene images of a rigidly moved copy of it at randomly drawn points (the
+    scene); returns (scene, model, the drawn point of each scene image)."""
     n, m, W, B, cs = c["points"].shape[0], c["m"], c["W"], float(c["bin_size"]), float(c["cos_s"])
     tp = torch.from_numpy(c["points"]).to(dev)
     tn = torch.from_numpy(c["normals"]).to(dev)
@@ -609,6 +610,14 @@ def bench_matching(spin, torch, dev, c, steps, warmup, stream, n_scene=16384, k=
     spin.si_generate(mesh, q, n_scene, W, B, cs, spin.make_schedule("FAC"), scene, stream)
     torch.cuda.synchronize()
     spin.si_mesh_destroy(mesh)
+    return scene, model, q
+
+
+def bench_matching(spin, torch, dev, c, steps, warmup, stream, n_scene=16384, k=5):
+    """Spin-image matching: n_scene images of a rigidly moved copy of the bench
+    mesh against all images of the mesh (correlation over all bins, k best)."""
+    m, W = c["m"], c["W"]
+    scene, model, q = _matching_inputs(spin, torch, dev, c, n_scene, stream)
     idx = torch.empty((n_scene, k), dtype=torch.int32, device=dev)
     val = torch.empty((n_scene, k), dtype=torch.float32, device=dev)
     peaks, src = _measured_peaks()
@@ -895,6 +904,27 @@ def run_profile_case(args):
     print(json.dumps({"profile_case": args.profile_case, "workload": c["name"], "reps": args.reps}))
 
 
+def run_profile_match(args):
+    """A short run for profilers: `--profile-match` scene images of the
+    matching workload against the bench mesh's 100,000, `reps` BF16 calls."""
+    import torch
+
+    import paper_1811_00901_gb300 as spin
+    from paper_1811_00901_gb300 import _build
+    _build.build()
+    dev = torch.device("cuda", 0)
+    c = _workload()
+    stream = torch.cuda.current_stream(dev)
+    scene, model, _ = _matching_inputs(spin, torch, dev, c, args.profile_match, stream)
+    k = 5
+    idx = torch.empty((args.profile_match, k), dtype=torch.int32, device=dev)
+    val = torch.empty((args.profile_match, k), dtype=torch.float32, device=dev)
+    for _ in range(args.reps):
+        spin.si_match(scene, args.profile_match, model, c["m"], c["W"], k, "BF16", idx, val, stream)
+        torch.cuda.synchronize()
+    print(json.dumps({"profile_match": args.profile_match, "model_images": c["m"], "W": c["W"], "reps": args.reps}))
+
+
 def _small_workload(name):
     from paper_1811_00901_gb300 import workloads as wl
     if name == "sphere":
@@ -913,6 +943,8 @@ def main():
     ap.add_argument("--profile-case", default=None, choices=list(SCHEDULES),
                     help="run the workload `--reps` times under one schedule (for ncu)")
     ap.add_argument("--profile-workload", default="heightfield", choices=["heightfield", "sphere", "scene"])
+    ap.add_argument("--profile-match", type=int, default=0, metavar="N_SCENE",
+                    help="run BF16 matching of N_SCENE images `--reps` times (for ncu)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=15)
@@ -927,6 +959,9 @@ def main():
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.profile_match:
+        run_profile_match(args)
         return
     if args.warmup < 3:
         args.warmup = 3
