@@ -412,12 +412,13 @@ def run_ours(args):
             bench_single(spin, torch, dev, c, ex_steps, args.warmup, flush, stream, scheds={
                 "FAC": spin.make_schedule("FAC", **shape),
                 "FAC_PROB": spin.make_schedule("FAC_PROB", fac_cov=cov, **shape),
-                "AWF": spin.make_schedule("AWF", **shape)}), fac_cov=cov)
+                "AWF": spin.make_schedule("AWF", **shape),
+                "AF": spin.make_schedule("AF", **shape)}), fac_cov=cov)
         # heterogeneity emulation (Sec. 5.2's Type2 + Type1 runs): the first half
         # of the resident workers 3x slower, and they request first
         P = spin.si_default_workers(c["W"], spin.make_schedule("FAC", **shape))
         het = {k: spin.make_schedule(k, num_workers=P, slow_workers=P // 2, slowdown=3.0, fac_cov=cov, **shape)
-               for k in ("STATIC", "SS", "GSS", "FAC", "FAC_PROB", "AWF")}
+               for k in ("STATIC", "SS", "GSS", "FAC", "FAC_PROB", "AWF", "AF")}
         h = bench_single(spin, torch, dev, c, ex_steps, args.warmup, flush, stream, scheds=het)
         h["emulation"] = {"workers": P, "slow_workers": P // 2, "slowdown": 3.0, "slow_request_first": True}
         h["over_static"] = {k: v["images_per_s"] / h["by_schedule"]["STATIC"]["images_per_s"]
@@ -561,7 +562,7 @@ def bench_trace(spin, torch, dev, c, shape, stream, het=None):
     mesh = spin.si_mesh_create(tp, tn, n, stream)
     res = {}
     try:
-        for kind in ("STATIC", "SS", "GSS", "FAC"):
+        for kind in ("STATIC", "SS", "GSS", "FAC", "AWF", "AF"):
             sched = spin.make_schedule(kind, **shape, **(het or {}))
             P = spin.si_default_workers(W, sched) if not het else het["num_workers"]
             claims = torch.zeros((200000, 4), dtype=torch.int64, device=dev)

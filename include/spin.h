@@ -24,7 +24,7 @@
  *
  * Image loop scheduling (Sec. 2.2 and Algorithm 3): the loop over images is
  * run by persistent thread blocks ("workers") that take chunks of the loop
- * under STATIC, SS, GSS or FAC (and FAC_PROB, AWF).  The scheduled iteration
+ * under STATIC, SS, GSS or FAC (and FAC_PROB, AWF, AF).  The scheduled iteration
  * is one image GROUP:
  * `group` consecutive images (in grid order) that a worker generates together
  * against one shared stream of candidate points.
@@ -92,7 +92,17 @@ typedef enum si_sched_kind {
                              [0.05, 20]); chunk = max(min_chunk, round(w x batch chunk)).  Chunk
                              sizes depend on measured times and are decided on the device; every
                              group is still generated exactly once.  In a batched call every item
-                             must use it. */
+                             must use it. */,
+    SI_SCHED_AF = 6       /* adaptive factoring (Banicescu and Liu, 2000; an adaptive rule of the kind
+                             Sec. 2.2 leaves to future work): each worker measures the mean mu_i and
+                             variance sigma_i^2 of its time per group (on the device; a chunk's
+                             wall time, claim and any emulated slowdown included, spread over its
+                             groups) and, with R groups remaining, D = sum sigma_j^2 / mu_j and
+                             E = 1 / sum 1 / mu_j over the workers measured so far (scaled to all
+                             P), takes ceil((D + 2ER - sqrt(D^2 + 4DER)) / (2 mu_i)) groups; before
+                             its first chunk ends, ceil(R / (4P)).  Chunks are >= min_chunk and
+                             are decided on the device; every group is still generated exactly
+                             once.  In a batched call every item must use it. */
 } si_sched_kind;
 
 /* How a contributing pair is counted into its image. */
@@ -294,8 +304,8 @@ si_status si_chunk_table(int32_t kind, int64_t units, int32_t workers, int32_t m
 
 /* si_chunk_table for a whole schedule (kind, min_chunk and, for
  * SI_SCHED_FAC_PROB, fac_cov); si_chunk_table(kind, ...) is this with
- * fac_cov = 0.  SI_SCHED_AWF has no table (its chunks are decided on the
- * device): SI_ERR_INVALID. */
+ * fac_cov = 0.  SI_SCHED_AWF and SI_SCHED_AF have no table (their chunks are
+ * decided on the device): SI_ERR_INVALID. */
 si_status si_schedule_chunks(const si_schedule *schedule, int64_t units, int32_t workers, int64_t *starts,
                              int64_t capacity, int64_t *nsteps);
 

@@ -29,6 +29,19 @@ getChunk(DM, schedulingStep, N, workersCount) and hands out the range
   quantities are real numbers; they are evaluated in IEEE double in this
   order, and the ceiling taken of the double quotient.
 
+* AF -- adaptive factoring (Banicescu and Liu 2000), one of the "more
+  complex" rules the paper leaves to future work.  Worker i, whose time per
+  iteration has mean mu_i and variance sigma_i^2, asks for a chunk while R
+  iterations remain and receives
+  x_i = (D + 2 E R - sqrt(D^2 + 4 D E R)) / (2 mu_i),
+  D = sum_j sigma_j^2 / mu_j, E = 1 / sum_j 1 / mu_j (see ``af_chunk``).
+  With T = mu_i x_i, the chunk's expected time, T is the smaller root of
+  T^2 - (D + 2 E R) T + (E R)^2 = 0, i.e. T + sqrt(D T) = E R: the time of
+  the chunk plus a deviation allowance equals one worker's share of the
+  remaining work.  Without variance (D = 0) the chunk is the worker's
+  speed-weighted share of R, R (1 / mu_i) / sum_j (1 / mu_j).  The rule's
+  inputs are measured while the loop runs, so it has no chunk table.
+
 Readings common to all rules (Algorithm 3 leaves both implicit): the
 scheduling step advances by one per assignment, and every chunk is clamped to
 the iterations that remain.  ``min_chunk`` (>= 1) is a lower bound on the
@@ -54,6 +67,16 @@ def fac_prob_batch_chunk(batch, remaining, workers, cov):
     else:
         x = 2.0 + b * b + b * math.sqrt(b * b + 4.0)
     return int(math.ceil(remaining / (x * workers)))
+
+
+def af_chunk(mu_i, mus, variances, remaining):
+    """Adaptive factoring's chunk (real-valued, before rounding) for a worker
+    with mean iteration time ``mu_i``, given every worker's mean time ``mus``
+    and variance ``variances`` and ``remaining`` iterations (see AF)."""
+    d = sum(v / m for m, v in zip(mus, variances))
+    e = 1.0 / sum(1.0 / m for m in mus)
+    r = float(remaining)
+    return (d + 2.0 * e * r - math.sqrt(d * d + 4.0 * d * e * r)) / (2.0 * mu_i)
 
 
 def get_chunk(kind, step, remaining, n, workers, min_chunk=1, fac_batch=None, cov=0.0):

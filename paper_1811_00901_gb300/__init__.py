@@ -6,7 +6,7 @@ in C) plus seeded workload generators (``workloads``).
 """
 from ._binding import (  # noqa: F401
     SCHED_NAMES, SI_ERR_BUSY, SI_ERR_CUDA, SI_ERR_INVALID, SI_ERR_OOM, SI_ERR_OVERFLOW, SI_ERR_TIMEOUT, SI_OK,
-    SI_SCHED_AWF, SI_SCHED_FAC, SI_SCHED_FAC_PROB, SI_SCHED_GSS, SI_SCHED_SS, SI_SCHED_STATIC, SI_BIN_BILINEAR, SI_BIN_NEAREST,
+    SI_SCHED_AF, SI_SCHED_AWF, SI_SCHED_FAC, SI_SCHED_FAC_PROB, SI_SCHED_GSS, SI_SCHED_SS, SI_SCHED_STATIC, SI_BIN_BILINEAR, SI_BIN_NEAREST,
     BIN_NAMES, SpinError, batch_items, exported_names, load,
     make_schedule, si_candidate_rc2, si_candidate_rc2_binned, si_check_bounded_wait, si_match, SI_MATCH_FP32,
     SI_MATCH_BF16, si_chunk_table, si_schedule_chunks, si_default_workers, si_generate, si_generate_batched, si_generate_host,

@@ -15,9 +15,9 @@ LIB_PATH = os.path.join(HERE, "_lib", "libspin_gb300.so")
 SI_OK, SI_ERR_INVALID, SI_ERR_CUDA, SI_ERR_OOM, SI_ERR_OVERFLOW, SI_ERR_TIMEOUT, SI_ERR_BUSY = range(7)
 STATUS_NAMES = {0: "SI_OK", 1: "SI_ERR_INVALID", 2: "SI_ERR_CUDA", 3: "SI_ERR_OOM", 4: "SI_ERR_OVERFLOW",
                 5: "SI_ERR_TIMEOUT", 6: "SI_ERR_BUSY"}
-SI_SCHED_STATIC, SI_SCHED_SS, SI_SCHED_GSS, SI_SCHED_FAC, SI_SCHED_FAC_PROB, SI_SCHED_AWF = range(6)
+SI_SCHED_STATIC, SI_SCHED_SS, SI_SCHED_GSS, SI_SCHED_FAC, SI_SCHED_FAC_PROB, SI_SCHED_AWF, SI_SCHED_AF = range(7)
 SCHED_NAMES = {"STATIC": SI_SCHED_STATIC, "SS": SI_SCHED_SS, "GSS": SI_SCHED_GSS, "FAC": SI_SCHED_FAC,
-               "FAC_PROB": SI_SCHED_FAC_PROB, "AWF": SI_SCHED_AWF}
+               "FAC_PROB": SI_SCHED_FAC_PROB, "AWF": SI_SCHED_AWF, "AF": SI_SCHED_AF}
 SI_BIN_BILINEAR, SI_BIN_NEAREST = 0, 1
 BIN_NAMES = {"BILINEAR": SI_BIN_BILINEAR, "NEAREST": SI_BIN_NEAREST}
 

@@ -120,8 +120,9 @@ struct Plan {
     int slow_workers = 0;
     float slowdown = 1.0f;
     std::vector<int> binning;  // per item: si_binning
-    // adaptive weighted factoring: unit bases of the items and FAC2 batch chunks
+    // adaptive rules (AWF, AF): unit bases of the items; af: the rule is AF
     bool awf = false;
+    bool af = false;
     int awf_min_chunk = 1;
     std::vector<int> awf_ubase;
     bool all_static = true;
@@ -139,7 +140,7 @@ struct Plan {
     std::vector<int64_t> split_base, counts_off;
     int64_t split_images = 0;
     size_t o_ctr = 0, o_items = 0, o_pieces = 0, o_steps = 0, o_sitems = 0, o_sqbase = 0, o_split = 0,
-           o_split_items = 0, o_awf_ubase = 0, o_hist = 0, o_perm = 0, o_counts = 0,
+           o_split_items = 0, o_awf_ubase = 0, o_af = 0, o_hist = 0, o_perm = 0, o_counts = 0,
            total_bytes = 0;
     bool empty = false;
 };
@@ -232,18 +233,21 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
     p->split_base.push_back(p->split_images);
 
     // ---- the scheduled loop: steps made of pieces
-    int n_awf = 0, n_used = 0;
+    int n_awf = 0, n_af = 0, n_used = 0;
     for (int k = 0; k < nitems; ++k) {
         if (items[k].m > 0 && scheds[k].kind != SI_SCHED_STATIC) p->all_static = false;
         if (items[k].m > 0) {
             ++n_used;
             if (scheds[k].kind == SI_SCHED_AWF) ++n_awf;
+            if (scheds[k].kind == SI_SCHED_AF) ++n_af;
         }
     }
-    if (n_awf > 0 && n_awf != n_used) {
-        set_error("adaptive weighted factoring must be the rule of every item of a call");
+    if ((n_awf > 0 && n_awf != n_used) || (n_af > 0 && n_af != n_used)) {
+        set_error("an adaptive rule (AWF, AF) must be the rule of every item of a call");
         return SI_ERR_INVALID;
     }
+    p->af = n_af > 0;
+    n_awf += n_af;
     p->step_piece.assign(1, 0);
     if (n_awf > 0) {
         // one loop over the concatenated units, chunk sizes decided on the device
@@ -333,7 +337,8 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
     p->o_split = align_up(p->o_sqbase + sizeof(int64_t) * p->sqbase.size(), 256);
     p->o_split_items = align_up(p->o_split + sizeof(int64_t) * p->split_base.size(), 256);
     p->o_awf_ubase = align_up(p->o_split_items + sizeof(int) * p->split_items.size(), 256);
-    p->o_hist = align_up(p->o_awf_ubase + sizeof(int) * p->awf_ubase.size(), 256);
+    p->o_af = align_up(p->o_awf_ubase + sizeof(int) * p->awf_ubase.size(), 256);
+    p->o_hist = align_up(p->o_af + (p->af ? sizeof(AfWorker) * (size_t)p->workers : 0), 256);
     p->o_perm = align_up(p->o_hist + sizeof(int) * (p->htot + 1), 256);
     p->o_counts = align_up(p->o_perm + sizeof(int) * p->qtot, 256);
     p->total_bytes = align_up(p->o_counts + sizeof(int) * p->split_images, 256);
@@ -467,6 +472,10 @@ si_status record_batch(const Plan &p, const std::vector<si_batch_item> &items, c
         a.total_units = p.awf_ubase.back();
         a.unit_base = reinterpret_cast<const int *>(scratch + p.o_awf_ubase);
         a.min_chunk = p.awf_min_chunk;
+        if (p.af) {
+            a.af = 1;
+            a.af_workers = reinterpret_cast<AfWorker *>(scratch + p.o_af);
+        }
     }
     // heterogeneity emulation: at most every launched block is slow
     const int blocks = p.all_static ? p.nsteps : p.workers;

@@ -76,7 +76,7 @@ si_status check_item(const si_batch_item &it, const si_schedule &sc, int dev) {
         set_error("NULL output");
         return SI_ERR_INVALID;
     }
-    if (sc.kind < SI_SCHED_STATIC || sc.kind > SI_SCHED_AWF || sc.min_chunk < 0 || sc.num_workers < 0 ||
+    if (sc.kind < SI_SCHED_STATIC || sc.kind > SI_SCHED_AF || sc.min_chunk < 0 || sc.num_workers < 0 ||
         !valid_group(sc.group) || sc.grid_div < 0 || sc.grid_div > 16 || sc.slices < 0 || sc.slices > 64) {
         set_error("bad schedule (kind %d, min_chunk %d, workers %d, group %d, grid_div %d)", sc.kind, sc.min_chunk,
                   sc.num_workers, sc.group, sc.grid_div);

@@ -155,8 +155,21 @@ struct LaunchCounters {
     unsigned long long awf_next;     // AWF: next unit of the call's concatenated unit space
     unsigned long long awf_claims;   // AWF: chunks handed out
     double awf_rate_sum;             // AWF: sum of the measured worker rates (units per ns)
-    unsigned awf_rated;              // AWF: workers with a measured rate
+    unsigned awf_rated;              // AWF and AF: workers with a measurement
     unsigned pad;
+    double af_d_sum;                 // AF: sum over measured workers of sigma^2 / mu (ns)
+    double af_e_sum;                 // AF: sum over measured workers of 1 / mu (units per ns)
+};
+
+// Adaptive factoring: one worker's statistics of its per-unit times (ns), kept
+// in global memory by the worker's thread 0.  A unit's time is scaled by its
+// chunk's wall time over the chunk's summed unit times, so the claim overhead
+// and a slow worker's idle are spread over the units.
+struct AfWorker {
+    double sum, sumsq;  // scaled unit times of the finished chunks
+    double cs, cs2;     // unit times of the current chunk
+    double d, e;        // the worker's published sigma^2 / mu and 1 / mu (e = 0: none yet)
+    int n, cn;          // units in sum; units timed in the current chunk
 };
 
 struct LaunchArgs {
@@ -172,8 +185,11 @@ struct LaunchArgs {
     int slow_workers = 0;   // heterogeneity emulation: blocks 0..slow_workers-1 are slow and request first
     float slowdown = 1.0f;  // a slow block idles (slowdown - 1) x each step's time
     int modes = 0;          // tile-ring disciplines present (kModeBarrier | kModeProducer); 0 = both
-    // adaptive weighted factoring (chunk sizes decided on the device)
+    // adaptive rules (chunk sizes decided on the device): awf = 1 for AWF and
+    // AF, af = 1 for AF, whose per-worker statistics live in af_workers[gridDim.x]
     int awf = 0;
+    int af = 0;
+    AfWorker *af_workers = nullptr;
     int total_units = 0;             // units of all items
     const int *unit_base = nullptr;  // [nitems + 1]: first unit of each item in the concatenation
     int min_chunk = 1;

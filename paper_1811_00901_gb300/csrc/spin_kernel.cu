@@ -93,6 +93,7 @@ struct __align__(16) Header {
     int cur_r, cur_o;          // barrier mode: producer row cursor
     unsigned long long t_step;  // heterogeneity emulation: start of a slow block's step
     unsigned long long t_trace; // claim trace: start of the current claim's work
+    unsigned long long af_t_unit;  // adaptive factoring: start of the current unit
     // adaptive weighted factoring: this worker's claim and its measured rate
     int awf_lo, awf_hi;
     unsigned long long awf_t0;  // when the current chunk was claimed
@@ -849,6 +850,72 @@ __device__ void awf_claim(const LaunchArgs &a, Header &H, const int claim_iter, 
     H.claim = (int)s;
 }
 
+// Adaptive factoring (Banicescu and Liu's AF rule), the request half of
+// getChunk run on the device by thread 0 of a worker.  The chunk just
+// finished is folded into the worker's statistics of its per-unit time: each
+// unit time is scaled by the chunk's wall time over its summed unit times, so
+// the claim overhead and a slow worker's idle count as the worker's own.  The
+// worker then publishes sigma^2 / mu and 1 / mu into launch-wide sums and takes
+//   x_i = (D + 2 E R - sqrt(D^2 + 4 D E R)) / (2 mu_i),
+//   D = sum_j sigma_j^2 / mu_j,  E = 1 / sum_j 1 / mu_j,
+// units, R being the units that remain; the sums run over the workers
+// measured so far, scaled to all P.  x_i mu_i = T is the smaller root of
+// T + sqrt(D T) = E R: the chunk's expected time plus a deviation allowance
+// equals a worker's share of what remains.  Before a worker has measured a
+// chunk (and before any worker has) it takes AWF's first chunk, half of
+// FAC2's, ceil(R / (4P)).  Chunks are at least min_chunk.  Sets H.claim,
+// H.awf_lo and H.awf_hi.
+__device__ void af_claim(const LaunchArgs &a, Header &H, const int claim_iter, const bool first_slow) {
+    const uint64_t now = global_ns();
+    AfWorker &w = a.af_workers[blockIdx.x];
+    if (claim_iter > 0 && w.cn > 0) {
+        const double wall = (double)(now - H.awf_t0);
+        const double f = w.cs > 0.0 ? fmax(wall / w.cs, 1.0) : 1.0;
+        w.sum += f * w.cs;
+        w.sumsq += f * f * w.cs2;
+        w.n += w.cn;
+        w.cs = 0.0;
+        w.cs2 = 0.0;
+        w.cn = 0;
+        const double mu = fmax(w.sum / (double)w.n, 1.0);
+        const double var =
+            w.n > 1 ? fmax(w.sumsq / (double)w.n - mu * mu, 0.0) * ((double)w.n / (double)(w.n - 1)) : 0.0;
+        const double d = var / mu, e = 1.0 / mu;
+        atomicAdd(&a.ctr->af_d_sum, d - w.d);
+        atomicAdd(&a.ctr->af_e_sum, e - w.e);
+        if (w.e == 0.0) atomicAdd(&a.ctr->awf_rated, 1u);
+        w.d = d;
+        w.e = e;
+    }
+    const unsigned long long s =
+        first_slow ? (unsigned long long)blockIdx.x
+                   : (unsigned long long)a.slow_workers + atomicAdd(&a.ctr->awf_claims, 1ull);
+    const unsigned long long cur = *(volatile unsigned long long *)&a.ctr->awf_next;
+    const long long rem = cur >= (unsigned long long)a.total_units ? 0 : (long long)a.total_units - (long long)cur;
+    const double P = (double)gridDim.x;
+    long long chunk;
+    const unsigned rated = *(volatile unsigned *)&a.ctr->awf_rated;
+    const double dsum = *(volatile double *)&a.ctr->af_d_sum, esum = *(volatile double *)&a.ctr->af_e_sum;
+    if (w.e > 0.0 && rated > 0 && esum > 0.0) {
+        const double scale = P / (double)rated;
+        const double D = fmax(dsum, 0.0) * scale, E = 1.0 / (esum * scale), R = (double)rem;
+        const double x = (D + 2.0 * E * R - sqrt(D * D + 4.0 * D * E * R)) / (2.0 / w.e);
+        chunk = (long long)ceil(fmax(x, 0.0));
+    } else {
+        const long long div = 4ll * gridDim.x;
+        chunk = (rem + div - 1) / div;
+    }
+    chunk = max((long long)a.min_chunk, min(chunk, max(rem, 1ll)));
+    const unsigned long long lo = atomicAdd(&a.ctr->awf_next, (unsigned long long)chunk);
+    const int total = a.total_units;
+    H.awf_lo = lo >= (unsigned long long)total ? total : (int)lo;
+    H.awf_hi = lo >= (unsigned long long)total ? total : (int)min(lo + (unsigned long long)chunk,
+                                                                   (unsigned long long)total);
+    H.awf_last = H.awf_hi - H.awf_lo;
+    H.awf_t0 = now;
+    H.claim = (int)s;
+}
+
 // MODES: the paths compiled in (kModeBarrier | kModeProducer | kModeNearest),
 // plus kModeWide for a mixed launch that runs two blocks per SM;
 // a launch whose groups all use one discipline runs the instance without the
@@ -904,6 +971,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks_for<MODES>()) spin_kernel
         H.awf_units = 0.0;
         H.awf_ns = 0.0;
         H.awf_rate = 0.0;
+        if (a.af) a.af_workers[blockIdx.x] = AfWorker{};
     }
 
     // generates units [u0, u1) of item `item`; `step` is the claim they came from
@@ -911,6 +979,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks_for<MODES>()) spin_kernel
         const ItemDesc &it = a.items[item];
         const int key = it.W * 8 + it.log2S;
         for (int u = u0; u < u1 && alive; ++u) {
+            if (a.af && tid == 0) H.af_t_unit = global_ns();
             // specialised shapes for the common widths, a runtime one otherwise
             // (the nearest-bin count: W = 32 in groups of 16, else the runtime shape)
             if ((MODES & kModeNearest) != 0 && it.binning == SI_BIN_NEAREST) {
@@ -954,6 +1023,14 @@ __global__ void __launch_bounds__(kThreads, min_blocks_for<MODES>()) spin_kernel
                     }
                 }
             }
+            if (a.af && tid == 0) {
+                // process_group ends on a block barrier: the unit's work is done
+                AfWorker &aw = a.af_workers[blockIdx.x];
+                const double t = (double)(global_ns() - H.af_t_unit);
+                aw.cs += t;
+                aw.cs2 += t * t;
+                ++aw.cn;
+            }
         }
     };
 
@@ -961,7 +1038,9 @@ __global__ void __launch_bounds__(kThreads, min_blocks_for<MODES>()) spin_kernel
         __syncthreads();
         if (tid == 0) {
             const bool first_slow = (int)blockIdx.x < a.slow_workers && claim_iter == 0;
-            if (a.awf) {
+            if (a.af) {
+                af_claim(a, H, claim_iter, first_slow);
+            } else if (a.awf) {
                 awf_claim(a, H, claim_iter, first_slow);
             } else {
                 int s;
@@ -1050,6 +1129,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks_for<MODES>()) spin_kernel
             atomicExch(&a.ctr->awf_claims, 0ull);
             atomicExch(reinterpret_cast<unsigned long long *>(&a.ctr->awf_rate_sum), 0ull);  // +0.0
             atomicExch(&a.ctr->awf_rated, 0u);
+            atomicExch(reinterpret_cast<unsigned long long *>(&a.ctr->af_d_sum), 0ull);
+            atomicExch(reinterpret_cast<unsigned long long *>(&a.ctr->af_e_sum), 0ull);
             atomicExch(&a.ctr->done_blocks, 0ull);
         }
     }

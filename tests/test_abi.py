@@ -99,6 +99,10 @@ def test_invalid_chunk_table_args(lib):
     assert lib.si_schedule_chunks(ctypes.byref(bad), 10, 2, None, 0, ctypes.byref(n)) != 0
     bad = spin.make_schedule("FAC_PROB", fac_cov=float("nan"))
     assert lib.si_schedule_chunks(ctypes.byref(bad), 10, 2, None, 0, ctypes.byref(n)) != 0
+    # the adaptive rules decide their chunks on the device: no table
+    for kind in ("AWF", "AF"):
+        sc = spin.make_schedule(kind)
+        assert lib.si_schedule_chunks(ctypes.byref(sc), 10, 2, None, 0, ctypes.byref(n)) != 0
 
 
 def test_tuning_table_json_round_trip(lib, tmp_path):

@@ -1,8 +1,9 @@
 """The scheduling extensions: probabilistic factoring (FAC_PROB), adaptive
-weighted factoring (AWF, chunk sizes decided on the device) and the
-heterogeneity emulation of the paper's Type1 + Type2 runs (Sec. 5.2).  None
-may change an image; FAC_PROB's steps follow its chunk table; AWF hands out
-every group exactly once; slow workers take the first steps."""
+weighted factoring and adaptive factoring (AWF, AF: chunk sizes decided on the
+device) and the heterogeneity emulation of the paper's Type1 + Type2 runs
+(Sec. 5.2).  None may change an image; FAC_PROB's steps follow its chunk
+table; AWF and AF hand out every group exactly once; slow workers take the
+first steps."""
 import numpy as np
 import pytest
 
@@ -46,7 +47,7 @@ def test_fac_prob_images_and_steps():
             assert per_step[s] == max(0, hi - lo), (cov, s)
 
 
-@pytest.mark.parametrize("kind", ["STATIC", "SS", "GSS", "FAC", "FAC_PROB", "AWF"])
+@pytest.mark.parametrize("kind", ["STATIC", "SS", "GSS", "FAC", "FAC_PROB", "AWF", "AF"])
 def test_slow_workers_change_no_image_and_take_the_first_steps(kind):
     import paper_1811_00901_gb300 as spin
     pts, nrm = wl.heightfield(6000, 12)
@@ -119,16 +120,17 @@ def test_slow_workers_slow_static_down_more_than_self_scheduling():
         spin.si_mesh_destroy(mesh)
 
 
+@pytest.mark.parametrize("kind", ["AWF", "AF"])
 @pytest.mark.parametrize("group,workers,slices,mc", [(8, 0, 1, 1), (1, 37, 0, 1), (32, 300, 1, 3), (4, 9, 4, 2)])
-def test_awf_generates_every_group_once(group, workers, slices, mc):
-    """AWF: images equal STATIC's; each image comes from exactly one claim and
-    the claims' images form contiguous group ranges of the loop."""
+def test_adaptive_rules_generate_every_group_once(kind, group, workers, slices, mc):
+    """AWF and AF: images equal STATIC's; each image comes from exactly one
+    claim, and each claim is one worker's."""
     import paper_1811_00901_gb300 as spin
     pts, nrm = wl.heightfield(5000, 31)
     W, B, c = 16, 0.02, 0.5
     ref, _ = gpu_run(pts, nrm, W, B, c, schedule=spin.make_schedule("STATIC"))
     img, pr = gpu_run(pts, nrm, W, B, c, probe=True,
-                      schedule=spin.make_schedule("AWF", group=group, num_workers=workers, slices=slices,
+                      schedule=spin.make_schedule(kind, group=group, num_workers=workers, slices=slices,
                                                   min_chunk=mc))
     np.testing.assert_array_equal(img, ref)
     assert (pr["step"] >= 0).all() and (pr["worker"] >= 0).all()
@@ -137,7 +139,8 @@ def test_awf_generates_every_group_once(group, workers, slices, mc):
         assert len(np.unique(pr["worker"][pr["step"] == s])) == 1
 
 
-def test_awf_batched_items_share_one_loop():
+@pytest.mark.parametrize("kind", ["AWF", "AF"])
+def test_adaptive_batched_items_share_one_loop(kind):
     import torch
 
     import paper_1811_00901_gb300 as spin
@@ -152,7 +155,7 @@ def test_awf_batched_items_share_one_loop():
             out = torch.empty((n, W, W), dtype=torch.int32, device=dev)
             items.append(dict(mesh=mh, query_idx=None, m=n, W=W, bin_size=B, cos_s=cs, out=out))
             refs.append(gpu_run(pts, nrm, W, B, cs, m=n, schedule=spin.make_schedule("STATIC"))[0])
-        spin.si_generate_batched(items, spin.make_schedule("AWF"))
+        spin.si_generate_batched(items, spin.make_schedule(kind))
         torch.cuda.synchronize()
         for it, ref in zip(items, refs):
             np.testing.assert_array_equal(it["out"].cpu().numpy(), ref)
@@ -194,8 +197,11 @@ def test_awf_balances_slow_workers():
         static = kernel_ms(spin.make_schedule("STATIC", num_workers=P, group=8, slow_workers=P // 2, slowdown=4.0))
         fac = kernel_ms(spin.make_schedule("FAC", num_workers=P, group=8, slow_workers=P // 2, slowdown=4.0))
         awf = kernel_ms(spin.make_schedule("AWF", num_workers=P, group=8, slow_workers=P // 2, slowdown=4.0))
+        af = kernel_ms(spin.make_schedule("AF", num_workers=P, group=8, slow_workers=P // 2, slowdown=4.0))
+        print("slow-worker balance (ms): STATIC %.3f FAC %.3f AWF %.3f AF %.3f" % (static, fac, awf, af))
         assert awf <= 0.7 * static, (awf, static)
         assert awf < fac, (awf, fac)
+        assert af <= 0.7 * static, (af, static)
     finally:
         spin.si_mesh_destroy(mesh)
 

@@ -98,3 +98,49 @@ def test_fac_prob_batches(n, P):
             rem -= sum(seq[b: b + P])
     f = [dls.chunk_sequence(dls.FAC_PROB, n, P, cov=cov)[0] for cov in (0.0, 0.5, 1.0, 2.0, 8.0)]
     assert all(y <= x for x, y in zip(f, f[1:]))
+
+
+def test_af_without_variance_is_the_speed_weighted_share():
+    """D = 0: the chunk is R (1 / mu_i) / sum_j (1 / mu_j), so one request per
+    worker hands out exactly R, each worker in proportion to its speed (for
+    equal speeds GSS's R / P)."""
+    mus = [1.0, 2.0, 4.0, 0.5]
+    R = 1000
+    xs = [dls.af_chunk(m, mus, [0.0] * 4, R) for m in mus]
+    assert abs(sum(xs) - R) < 1e-9
+    inv = [1.0 / m for m in mus]
+    for x, w in zip(xs, inv):
+        assert abs(x - R * w / sum(inv)) < 1e-9
+    assert abs(dls.af_chunk(3.0, [3.0] * 8, [0.0] * 8, 800) - 100.0) < 1e-12
+
+
+def test_af_hand_evaluated():
+    """Two workers, mu = (1, 2), sigma^2 = (1, 4), R = 10, by hand: D = 1/1 +
+    4/2 = 3, E = 1 / (1 + 1/2) = 2/3, ER = 20/3; worker 1 gets
+    (3 + 40/3 - sqrt(9 + 80)) / 2 = 3.44968..., worker 2 half that."""
+    x1 = dls.af_chunk(1.0, [1.0, 2.0], [1.0, 4.0], 10)
+    x2 = dls.af_chunk(2.0, [1.0, 2.0], [1.0, 4.0], 10)
+    assert abs(x1 - (3.0 + 40.0 / 3.0 - 89.0 ** 0.5) / 2.0) < 1e-12
+    assert abs(x1 - 3.4496761) < 1e-6
+    assert abs(x2 - x1 / 2.0) < 1e-12
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_af_chunk_time_plus_deviation_is_the_share_of_the_rest(seed):
+    """T = mu_i x_i satisfies T + sqrt(D T) = E R with 0 <= T <= E R; larger
+    variances give smaller chunks; the chunk grows with R."""
+    import random
+    rng = random.Random(seed)
+    P = rng.randint(1, 64)
+    mus = [rng.uniform(0.1, 10.0) for _ in range(P)]
+    var = [rng.uniform(0.0, 4.0) * m * m for m in mus]
+    R = rng.randint(1, 100_000)
+    i = rng.randrange(P)
+    x = dls.af_chunk(mus[i], mus, var, R)
+    D = sum(v / m for m, v in zip(mus, var))
+    E = 1.0 / sum(1.0 / m for m in mus)
+    T = mus[i] * x
+    assert 0.0 <= T <= E * R * (1 + 1e-12)
+    assert abs(T + (D * T) ** 0.5 - E * R) <= 1e-9 * E * R
+    assert dls.af_chunk(mus[i], mus, [2.0 * v + 0.1 for v in var], R) < x
+    assert dls.af_chunk(mus[i], mus, var, 2 * R) > x
