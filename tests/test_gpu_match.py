@@ -171,3 +171,43 @@ def test_tensor_core_padded_width():
         out = np.ones(n_model, bool)
         out[idx[i]] = False
         assert r[i, out].max() <= r[i, idx[i, k - 1]] + 2 * tol
+
+
+@pytest.mark.parametrize("precision", ["BF16", "FP32"])
+def test_misaligned_images_take_the_scalar_centring(precision):
+    """Images whose rows are 16-byte aligned are centred four pixels per lane
+    step; images at a 4-byte offset take the one-pixel path.  Both must give
+    the same lists (they differ only in the order of the FP32 sum of squares
+    of each image, a relative 1e-6 of its norm)."""
+    import torch
+
+    import paper_1811_00901_gb300 as spin
+    rng = np.random.default_rng(77)
+    W, k, n_scene, n_model = 32, 5, 300, 4000
+    model = ((rng.random((n_model, W, W)) < 0.4) * rng.integers(0, 50 * 65536, (n_model, W, W))).astype(np.int32)
+    scene = model[rng.integers(0, n_model, n_scene)].copy()
+    scene += ((rng.random(scene.shape) < 0.05) * rng.integers(0, 65536 * 8, scene.shape)).astype(np.int32)
+    dev = torch.device("cuda:0")
+    out = {}
+    for off in (0, 1):
+        bs = torch.zeros(scene.size + off, dtype=torch.int32, device=dev)
+        bm = torch.zeros(model.size + off, dtype=torch.int32, device=dev)
+        ts, tm = bs[off:].view(n_scene, W, W), bm[off:].view(n_model, W, W)
+        ts.copy_(torch.from_numpy(scene))
+        tm.copy_(torch.from_numpy(model))
+        assert (ts.data_ptr() % 16 == 0) == (off == 0)
+        idx = torch.full((n_scene, k), -3, dtype=torch.int32, device=dev)
+        val = torch.zeros((n_scene, k), dtype=torch.float32, device=dev)
+        spin.si_match(ts, n_scene, tm, n_model, W, k, precision, idx, val)
+        torch.cuda.synchronize()
+        out[off] = (idx.cpu().numpy(), val.cpu().numpy())
+    (i0, v0), (i1, v1) = out[0], out[1]
+    # a last-bit change of an image's norm can move a BF16 operand by one unit
+    # (about 1e-4 of a pixel of a unit image of 1,024): a few 1e-6 per list value
+    assert np.all(np.abs(v0 - v1) <= (1e-4 if precision == "BF16" else 1e-5))
+    r = match.correlations(scene, model)
+    for q in range(n_scene):
+        sv = np.sort(r[q])[::-1]
+        for t in range(k):
+            if sv[t] - sv[t + 1] > 1e-3 and (t == 0 or sv[t - 1] - sv[t] > 1e-3):
+                assert i0[q, t] == i1[q, t], (q, t)
