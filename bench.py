@@ -279,10 +279,11 @@ def run_ours(args):
     shape = dict(group=tuned.group, grid_div=tuned.grid_div)
     configs = {name: spin.make_schedule(name, **shape) for name in SCHEDULES}
     configs["tuned"] = spin.make_schedule(tuned.kind, min_chunk=tuned.min_chunk, num_workers=tuned.num_workers,
-                                          **shape)
+                                          order=tuned.order, **shape)
     tuned_desc = {"kind": [k for k, v in spin.SCHED_NAMES.items() if v == tuned.kind][0],
                   "min_chunk": tuned.min_chunk, "num_workers": tuned.num_workers, "group": tuned.group,
-                  "grid_div": tuned.grid_div}
+                  "grid_div": tuned.grid_div,
+                  "order": "decreasing estimated cost" if tuned.order else "grid"}
 
     results = {}
     clocks = ClockSampler(local)

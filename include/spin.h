@@ -134,6 +134,12 @@ typedef struct si_schedule {
                             emulation comes from the override (or the first item's rule). */
     float slowdown;      /* >= 1 (0 -> 1) */
     float fac_cov;       /* SI_SCHED_FAC_PROB: sigma / mu of an iteration's time, finite, >= 0 */
+    int32_t order;       /* order in which the dynamic rules hand out the groups: 0 -> grid order
+                            (the loop as written); 1 -> decreasing estimated cost (the number of
+                            candidates in each group's grid stencil, bucketed by 2^(1/32)), so
+                            the cheapest groups come last and the last chunks balance the
+                            workers' finishing times.  The estimate costs three small kernels per
+                            call.  Results are unchanged.  STATIC always runs grid order. */
 } si_schedule;
 
 /* Optional per-image probes (device buffers of m entries, each may be NULL).
@@ -283,8 +289,8 @@ si_status si_generate_host(const float *points, const float *normals, int64_t n,
  *   The mesh's grid for this W, bin size and grid_div must exist already
  *   (si_mesh_prepare); otherwise SI_ERR_INVALID.
  *   Schedules: STATIC, SS, GSS or FAC with bilinear binning, no slow
- *   workers and one slice per group (slices 0 or 1); anything else is
- *   SI_ERR_INVALID.
+ *   workers, one slice per group (slices 0 or 1) and grid order (order 0);
+ *   anything else is SI_ERR_INVALID.
  *   The first call on a device (with it current) looks up the array's device
  *   address; make that first call before any stream capture.
  *   Calls share the array: two calls whose work overlaps on the GPU race. */

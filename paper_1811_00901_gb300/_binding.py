@@ -32,7 +32,7 @@ class si_schedule(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("min_chunk", ctypes.c_int32), ("num_workers", ctypes.c_int32),
                 ("group", ctypes.c_int32), ("grid_div", ctypes.c_int32), ("slices", ctypes.c_int32),
                 ("binning", ctypes.c_int32), ("slow_workers", ctypes.c_int32), ("slowdown", ctypes.c_float),
-                ("fac_cov", ctypes.c_float)]
+                ("fac_cov", ctypes.c_float), ("order", ctypes.c_int32)]
 
 
 class si_probe(ctypes.Structure):
@@ -163,13 +163,13 @@ def _ptr(t):
 
 
 def make_schedule(kind="GSS", min_chunk=1, num_workers=0, group=0, grid_div=0, slices=0, binning=0,
-                  slow_workers=0, slowdown=0.0, fac_cov=0.0):
+                  slow_workers=0, slowdown=0.0, fac_cov=0.0, order=0):
     if isinstance(kind, str):
         kind = SCHED_NAMES[kind.upper()]
     if isinstance(binning, str):
         binning = BIN_NAMES[binning.upper()]
     return si_schedule(int(kind), int(min_chunk), int(num_workers), int(group), int(grid_div), int(slices),
-                       int(binning), int(slow_workers), float(slowdown), float(fac_cov))
+                       int(binning), int(slow_workers), float(slowdown), float(fac_cov), int(order))
 
 
 # ----------------------------------------------------------------------------

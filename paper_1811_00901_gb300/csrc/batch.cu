@@ -123,6 +123,10 @@ struct Plan {
     // adaptive rules (AWF, AF): unit bases of the items; af: the rule is AF
     bool awf = false;
     bool af = false;
+    // cost order (si_schedule.order = 1): the ordered items and their first
+    // group in the concatenated group space
+    std::vector<int> ord;  // ord_items, then gbase[n_ord + 1]
+    int n_ord = 0, ord_groups = 0;
     int awf_min_chunk = 1;
     std::vector<int> awf_ubase;
     bool all_static = true;
@@ -140,7 +144,8 @@ struct Plan {
     std::vector<int64_t> split_base, counts_off;
     int64_t split_images = 0;
     size_t o_ctr = 0, o_items = 0, o_pieces = 0, o_steps = 0, o_sitems = 0, o_sqbase = 0, o_split = 0,
-           o_split_items = 0, o_awf_ubase = 0, o_af = 0, o_hist = 0, o_perm = 0, o_counts = 0,
+           o_split_items = 0, o_awf_ubase = 0, o_af = 0, o_ord = 0, o_hist = 0, o_perm = 0, o_counts = 0,
+           o_gorder = 0, o_gkey = 0, o_ghist = 0,
            total_bytes = 0;
     bool empty = false;
 };
@@ -300,6 +305,23 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
     }
     if (!p->awf) p->nsteps = (int)p->step_piece.size() - 1;
 
+    // ---- cost order of the groups of the dynamic rules' items that ask for it
+    {
+        std::vector<int> oi, gb(1, 0);
+        for (int k = 0; k < nitems; ++k) {
+            if (items[k].m == 0 || scheds[k].order != 1 || scheds[k].kind == SI_SCHED_STATIC || p->all_static)
+                continue;
+            const int groups = p->units[k] / p->slices[k];
+            if (groups < 2) continue;
+            oi.push_back(k);
+            gb.push_back(gb.back() + groups);
+        }
+        p->n_ord = (int)oi.size();
+        p->ord_groups = gb.back();
+        p->ord = oi;
+        if (p->n_ord > 0) p->ord.insert(p->ord.end(), gb.begin(), gb.end());
+    }
+
     // ---- query sorting (items that are not "all points of the mesh")
     p->sort_of.assign(nitems, -1);
     for (int k = 0; k < nitems; ++k) {
@@ -338,10 +360,14 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
     p->o_split_items = align_up(p->o_split + sizeof(int64_t) * p->split_base.size(), 256);
     p->o_awf_ubase = align_up(p->o_split_items + sizeof(int) * p->split_items.size(), 256);
     p->o_af = align_up(p->o_awf_ubase + sizeof(int) * p->awf_ubase.size(), 256);
-    p->o_hist = align_up(p->o_af + (p->af ? sizeof(AfWorker) * (size_t)p->workers : 0), 256);
+    p->o_ord = align_up(p->o_af + (p->af ? sizeof(AfWorker) * (size_t)p->workers : 0), 256);
+    p->o_hist = align_up(p->o_ord + sizeof(int) * p->ord.size(), 256);
     p->o_perm = align_up(p->o_hist + sizeof(int) * (p->htot + 1), 256);
     p->o_counts = align_up(p->o_perm + sizeof(int) * p->qtot, 256);
-    p->total_bytes = align_up(p->o_counts + sizeof(int) * p->split_images, 256);
+    p->o_gorder = align_up(p->o_counts + sizeof(int) * p->split_images, 256);
+    p->o_gkey = align_up(p->o_gorder + sizeof(int) * (size_t)p->ord_groups, 256);
+    p->o_ghist = align_up(p->o_gkey + sizeof(uint16_t) * (size_t)p->ord_groups, 256);
+    p->total_bytes = align_up(p->o_ghist + sizeof(int) * (size_t)p->n_ord * kCostBuckets, 256);
     return SI_OK;
 }
 
@@ -400,6 +426,8 @@ void fill_blob(const Plan &p, const std::vector<si_batch_item> &items, const std
     int *d_counts = reinterpret_cast<int *>(scratch + p.o_counts);
     for (int k = 0; k < p.nitems; ++k) descs[k].slices = p.slices[k];
     for (size_t s = 0; s < p.split_items.size(); ++s) descs[p.split_items[s]].counts = d_counts + p.counts_off[s];
+    int *d_gorder = reinterpret_cast<int *>(scratch + p.o_gorder);
+    for (int j = 0; j < p.n_ord; ++j) descs[p.ord[j]].gorder = d_gorder + p.ord[p.n_ord + j];
     char *h = blob->data();
     std::memcpy(h, descs.data(), sizeof(ItemDesc) * p.nitems);
     std::memcpy(h + (p.o_pieces - p.o_items), p.pieces.data(), sizeof(Piece) * p.pieces.size());
@@ -415,6 +443,7 @@ void fill_blob(const Plan &p, const std::vector<si_batch_item> &items, const std
     if (p.awf) {
         std::memcpy(h + (p.o_awf_ubase - p.o_items), p.awf_ubase.data(), sizeof(int) * p.awf_ubase.size());
     }
+    if (p.n_ord > 0) std::memcpy(h + (p.o_ord - p.o_items), p.ord.data(), sizeof(int) * p.ord.size());
 }
 
 // Device commands of a planned batch on `stream` (also what a graph captures).
@@ -455,6 +484,18 @@ si_status record_batch(const Plan &p, const std::vector<si_batch_item> &items, c
                                                                        p.qtot, hist, perm);
         ++nk;
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "query sort");
+    }
+    if (p.n_ord > 0) {
+        // the query order (above) first: the cost estimate reads each group's queries
+        const int *d_ord = reinterpret_cast<const int *>(scratch + p.o_ord);
+        int kk = 0;
+        si_status st = enqueue_group_order(reinterpret_cast<const ItemDesc *>(scratch + p.o_items), d_ord,
+                                           d_ord + p.n_ord, p.n_ord, p.ord_groups,
+                                           reinterpret_cast<uint16_t *>(scratch + p.o_gkey),
+                                           reinterpret_cast<int *>(scratch + p.o_ghist),
+                                           reinterpret_cast<int *>(scratch + p.o_gorder), stream, &kk);
+        if (st != SI_OK) return st;
+        nk += kk;
     }
     LaunchArgs a;
     a.items = reinterpret_cast<const ItemDesc *>(scratch + p.o_items);

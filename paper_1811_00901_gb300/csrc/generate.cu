@@ -84,9 +84,9 @@ si_status check_item(const si_batch_item &it, const si_schedule &sc, int dev) {
     }
     if ((sc.binning != SI_BIN_BILINEAR && sc.binning != SI_BIN_NEAREST) || sc.slow_workers < 0 ||
         !(sc.slowdown == 0.0f || (sc.slowdown >= 1.0f && sc.slowdown <= 1000.0f)) ||
-        !(sc.fac_cov >= 0.0f && sc.fac_cov <= 1e6f)) {
-        set_error("bad schedule (binning %d, slow_workers %d, slowdown %g, fac_cov %g)", sc.binning,
-                  sc.slow_workers, (double)sc.slowdown, (double)sc.fac_cov);
+        !(sc.fac_cov >= 0.0f && sc.fac_cov <= 1e6f) || sc.order < 0 || sc.order > 1) {
+        set_error("bad schedule (binning %d, slow_workers %d, slowdown %g, fac_cov %g, order %d)", sc.binning,
+                  sc.slow_workers, (double)sc.slowdown, (double)sc.fac_cov, sc.order);
         return SI_ERR_INVALID;
     }
     const int l2 = choose_log2_group(it.W, sc.group);

@@ -141,7 +141,20 @@ struct ItemDesc {
     int *counts;  // [m], zeroed, when slices > 1
     int binning;  // si_binning: SI_BIN_NEAREST counts 1 per pair at (ceil(u), ceil(v))
     float B;      // bin size (the nearest-bin count divides by it)
+    const int *gorder;  // [groups] loop position -> group (decreasing estimated cost), or null: grid order
 };
+
+// Cost order of the groups (si_schedule.order = 1): for the `n_ord` items
+// ord_items[0..n_ord) of a launch, whose groups occupy [gbase[j], gbase[j+1])
+// of a concatenated group space, estimate each group's cost (the candidates
+// of its stencil), bucket it by log cost and write each item's groups in
+// decreasing bucket order to gorder[gbase[j] ..].  Scratch: key[gbase[n_ord]]
+// and hist[n_ord * kCostBuckets].  Four stream-ordered operations (a memset
+// and three kernels); returns the kernels launched in *kernels.
+constexpr int kCostBuckets = 1024;
+si_status enqueue_group_order(const ItemDesc *items, const int *ord_items, const int *gbase, int n_ord,
+                              int total_groups, uint16_t *key, int *hist, int *gorder, cudaStream_t st,
+                              int *kernels);
 
 // A piece of the scheduled loop: units [u0, u1) of item `item`.
 struct Piece {

@@ -133,9 +133,9 @@ extern "C" si_status si_generate_noalloc(si_mesh_t mesh, const int32_t *query_id
     si_status s = check_item(it, schedule, dev);
     if (s != SI_OK) return s;
     if (schedule.kind >= SI_SCHED_FAC_PROB || schedule.binning != SI_BIN_BILINEAR || schedule.slow_workers != 0 ||
-        schedule.slices > 1) {
-        set_error("si_generate_noalloc: takes STATIC, SS, GSS or FAC, bilinear binning, no slow workers and one "
-                  "slice per group");
+        schedule.slices > 1 || schedule.order != 0) {
+        set_error("si_generate_noalloc: takes STATIC, SS, GSS or FAC, bilinear binning, no slow workers, one "
+                  "slice per group and grid order");
         return SI_ERR_INVALID;
     }
     if (m == 0) return SI_OK;

@@ -174,6 +174,58 @@ __device__ int block_scan_rows(const int *len, int *off, int nr, Header &H) {
     return total;
 }
 
+// ---- the candidate stencil of a group (used by process_group and by the
+// cost estimate of group_cost_kernel, so both see the same cells)
+
+// Safety margin of the stencil: a few ulps of the coordinates and of the radius.
+__device__ __forceinline__ float stencil_margin(const GridGeom &gg, float Rc) {
+    return 1e-5f * (gg.mag + Rc + gg.cell_len) + 1e-30f;
+}
+
+// The y and z cell ranges within Rc (plus margin) of the box [lo, hi].
+__device__ __forceinline__ void stencil_yz(float oy, float oz, float inv, int dy_, int dz_, float lo1, float lo2,
+                                           float hi1, float hi2, float Rc, float margin, int &ylo, int &yhi,
+                                           int &zlo, int &zhi) {
+    const float r = Rc + margin;
+    ylo = cell_coord(lo1 - r, oy, inv, dy_);
+    yhi = cell_coord(hi1 + r, oy, inv, dy_);
+    zlo = cell_coord(lo2 - r, oz, inv, dz_);
+    zhi = cell_coord(hi2 + r, oz, inv, dz_);
+}
+
+// Cells [c0, c0 + n) of stencil row (y, z): the cells of the row within the
+// candidate radius (Rc2, plus margin) of the box [gmin, gmax]; n = 0 when the
+// row misses it.
+__device__ __forceinline__ int stencil_row(float ox, float oy, float oz, float cell, float inv, int dx_, int dy_,
+                                           const float *gmin, const float *gmax, float Rc2, float margin, int y,
+                                           int z, int &c0) {
+    const float sy0 = fmaf((float)y, cell, oy), sy1 = sy0 + cell;
+    const float sz0 = fmaf((float)z, cell, oz), sz1 = sz0 + cell;
+    const float gy = fmaxf(0.0f, fmaxf(sy0 - gmax[1], gmin[1] - sy1) - margin);
+    const float gz = fmaxf(0.0f, fmaxf(sz0 - gmax[2], gmin[2] - sz1) - margin);
+    const float rem = Rc2 - gy * gy - gz * gz;
+    if (!(rem >= 0.0f)) return 0;
+    const float rx = sqrtf(rem) + margin;
+    const int x0 = cell_coord(gmin[0] - rx, ox, inv, dx_);
+    const int x1 = cell_coord(gmax[0] + rx, ox, inv, dx_);
+    c0 = (z * dy_ + y) * dx_ + x0;
+    return x1 - x0 + 1;
+}
+
+// Query t of an item (in grid order): its output slot q, whether its index is
+// valid, and its position in the grid's sorted points.
+__device__ __forceinline__ int query_sorted_pos(const ItemDesc &it, int64_t t, int &q, bool &ok) {
+    q = it.perm ? it.perm[t] : (int)t;
+    int sp = (int)t;
+    ok = true;
+    if (!it.perm_is_grid) {
+        const int src = it.query_idx ? it.query_idx[q] : q;
+        ok = (unsigned)src < (unsigned)it.n_points;
+        sp = ok ? it.sorted_pos[src] : 0;
+    }
+    return sp;
+}
+
 // Constants of one item that the pair evaluation needs (and, for the
 // SI_DEBUG_BOUNDS build, the group's image words and the item's flags).
 struct PairConsts {
@@ -446,8 +498,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
     const int dx_ = gg.dims[0], dy_ = gg.dims[1], dz_ = gg.dims[2];
     PairConsts k{it.Rc2, it.cosS, it.invB, it.halfW, it.umax, it.B, nullptr, 0, it.flags};
     const float Rc = it.Rc;
-    // stencil safety margin: a few ulps of the coordinates and of the radius
-    const float margin = 1e-5f * (gg.mag + Rc + gg.cell_len) + 1e-30f;
+    const float margin = stencil_margin(gg, Rc);
     const int slot = lane & (S - 1);
     // candidates per tile: a compile-time constant for the specialised shapes
     constexpr int TNC = WT > 0 ? tile_for_shape(WT, LS) : 0;
@@ -464,9 +515,11 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
 
     // unit u = slice `sl` of group `g`: with K slices per group, K blocks share
     // the group's candidate stream and add their partial images into `out`
+    // (with a cost order, loop position gi holds group gorder[gi])
     const int K = it.slices > 1 ? it.slices : 1;
-    const int g = K == 1 ? u : u / K;
-    const int sl = K == 1 ? 0 : u - g * K;
+    const int gi = K == 1 ? u : u / K;
+    const int sl = K == 1 ? 0 : u - gi * K;
+    const int g = it.gorder ? it.gorder[gi] : gi;
     const int64_t t0 = (int64_t)g * S;
     const int nq = (int)(m - t0 < (int64_t)S ? m - t0 : (int64_t)S);
     if (K > 1 && tid < 32) H.slot_cnt[tid] = 0;
@@ -474,14 +527,9 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
     if (tid < S) {
         if (tid < nq) {
             const int64_t t = t0 + tid;
-            const int q = it.perm ? it.perm[t] : (int)t;
-            int sp = (int)t;
-            bool ok = true;
-            if (!it.perm_is_grid) {
-                const int src = it.query_idx ? it.query_idx[q] : q;
-                ok = (unsigned)src < (unsigned)it.n_points;
-                sp = ok ? it.sorted_pos[src] : 0;
-            }
+            int q;
+            bool ok;
+            int sp = query_sorted_pos(it, t, q, ok);
             if (!ok) atomicOr(it.flags, kFlagBadQuery);
             if (!SI_IN_BOUNDS((unsigned)sp < (unsigned)it.n_points, it.flags)) sp = 0;
             Q[tid].p = pn[2 * (int64_t)sp];
@@ -529,11 +577,7 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
             H.gmax[0] = hi0;
             H.gmax[1] = hi1;
             H.gmax[2] = hi2;
-            const float r = Rc + margin;
-            H.ylo = cell_coord(lo1 - r, oy, inv, dy_);
-            H.yhi = cell_coord(hi1 + r, oy, inv, dy_);
-            H.zlo = cell_coord(lo2 - r, oz, inv, dz_);
-            H.zhi = cell_coord(hi2 + r, oz, inv, dz_);
+            stencil_yz(oy, oz, inv, dy_, dz_, lo1, lo2, hi1, hi2, Rc, margin, H.ylo, H.yhi, H.zlo, H.zhi);
         }
     }
     __syncthreads();
@@ -555,21 +599,12 @@ __device__ bool process_group(const ItemDesc &it, const int u, const int step, c
         for (int r = tid; r < nr; r += kThreads) {
             const int rr = rb + r;
             const int y = ylo + rr % ny, z = zlo + rr / ny;
-            const float sy0 = fmaf((float)y, cell, oy), sy1 = sy0 + cell;
-            const float sz0 = fmaf((float)z, cell, oz), sz1 = sz0 + cell;
-            const float gy = fmaxf(0.0f, fmaxf(sy0 - H.gmax[1], H.gmin[1] - sy1) - margin);
-            const float gz = fmaxf(0.0f, fmaxf(sz0 - H.gmax[2], H.gmin[2] - sz1) - margin);
-            const float rem = k.Rc2 - gy * gy - gz * gz;
+            int c0 = 0;
+            const int ncx = stencil_row(ox, oy, oz, cell, inv, dx_, dy_, H.gmin, H.gmax, k.Rc2, margin, y, z, c0);
             int start = 0, len = 0;
-            if (rem >= 0.0f) {
-                const float rx = sqrtf(rem) + margin;
-                const int x0 = cell_coord(H.gmin[0] - rx, ox, inv, dx_);
-                const int x1 = cell_coord(H.gmax[0] + rx, ox, inv, dx_);
-                const int c0 = (z * dy_ + y) * dx_ + x0;
-                if (SI_IN_BOUNDS(c0 >= 0 && x1 >= x0 && c0 + (x1 - x0) + 1 <= gg.ncell, it.flags)) {
-                    start = cstart[c0];
-                    len = cstart[c0 + (x1 - x0) + 1] - start;
-                }
+            if (ncx > 0 && SI_IN_BOUNDS(c0 >= 0 && c0 + ncx <= gg.ncell, it.flags)) {
+                start = cstart[c0];
+                len = cstart[c0 + ncx] - start;
             }
             sv.row_start[r] = start;
             sv.row_len[r] = len;
@@ -848,6 +883,114 @@ __device__ void awf_claim(const LaunchArgs &a, Header &H, const int claim_iter, 
     H.awf_last = H.awf_hi - H.awf_lo;
     H.awf_t0 = now;
     H.claim = (int)s;
+}
+
+// ---- cost order of the groups (si_schedule.order = 1)
+
+// One warp per group of the concatenated group space: the group's stencil
+// (its queries' bounding box, the rows and their cell ranges, exactly as
+// process_group builds it) and the number of candidates it streams, bucketed
+// as round(32 log2(candidates)) and stored as kCostBuckets - 1 - bucket, so
+// that an ascending pass over the keys visits the costliest groups first.
+__global__ void group_cost_kernel(const ItemDesc *__restrict__ items, const int *__restrict__ ord_items,
+                                  const int *__restrict__ gbase, int n_ord, int total_groups, uint16_t *key,
+                                  int *hist) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int G = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; G < total_groups; G += warps) {
+        int lo = 0, hi = n_ord - 1;  // the ordered item whose range holds G
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (gbase[mid] <= G)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const ItemDesc &it = items[ord_items[lo]];
+        const int g = G - gbase[lo];
+        const int S = 1 << it.log2S;
+        const int64_t t0 = (int64_t)g * S;
+        const int nq = (int)(it.m - t0 < (int64_t)S ? it.m - t0 : (int64_t)S);
+        float lo0 = INFINITY, lo1 = INFINITY, lo2 = INFINITY, hi0 = -INFINITY, hi1 = -INFINITY, hi2 = -INFINITY;
+        if (lane < nq) {
+            int q;
+            bool ok;
+            int sp = query_sorted_pos(it, t0 + lane, q, ok);
+            if ((unsigned)sp >= (unsigned)it.n_points) sp = 0;
+            const float4 p = it.pn[2 * (int64_t)sp];
+            lo0 = hi0 = p.x;
+            lo1 = hi1 = p.y;
+            lo2 = hi2 = p.z;
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            lo0 = fminf(lo0, __shfl_xor_sync(0xffffffffu, lo0, d));
+            lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, d));
+            lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, d));
+            hi0 = fmaxf(hi0, __shfl_xor_sync(0xffffffffu, hi0, d));
+            hi1 = fmaxf(hi1, __shfl_xor_sync(0xffffffffu, hi1, d));
+            hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, d));
+        }
+        const GridGeom &gg = *it.geom;
+        const float ox = gg.origin[0], oy = gg.origin[1], oz = gg.origin[2];
+        const float cell = gg.cell_len, inv = gg.inv_cell;
+        const int dx_ = gg.dims[0], dy_ = gg.dims[1], dz_ = gg.dims[2];
+        const float margin = stencil_margin(gg, it.Rc);
+        int ylo, yhi, zlo, zhi;
+        stencil_yz(oy, oz, inv, dy_, dz_, lo1, lo2, hi1, hi2, it.Rc, margin, ylo, yhi, zlo, zhi);
+        const float gmin[3] = {lo0, lo1, lo2}, gmax[3] = {hi0, hi1, hi2};
+        const int ny = yhi - ylo + 1, nrows = ny * (zhi - zlo + 1);
+        long long cand = 0;
+        for (int r = lane; r < nrows; r += 32) {
+            const int y = ylo + r % ny, z = zlo + r / ny;
+            int c0 = 0;
+            const int ncx = stencil_row(ox, oy, oz, cell, inv, dx_, dy_, gmin, gmax, it.Rc2, margin, y, z, c0);
+            if (ncx > 0 && c0 >= 0 && c0 + ncx <= gg.ncell) cand += it.cell_start[c0 + ncx] - it.cell_start[c0];
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) cand += __shfl_xor_sync(0xffffffffu, cand, d);
+        if (lane == 0) {
+            const int b = cand > 0 ? min(kCostBuckets - 1, __float2int_rn(32.0f * __log2f((float)cand))) : 0;
+            const int kb = kCostBuckets - 1 - b;
+            key[G] = (uint16_t)kb;
+            atomicAdd(hist + (int64_t)lo * kCostBuckets + kb, 1);
+        }
+    }
+}
+
+// One block per ordered item: the exclusive scan of its bucket counts, offset
+// by the item's first group, in place.
+__global__ void group_cost_scan_kernel(const int *__restrict__ gbase, int *hist) {
+    __shared__ int part[kCostBuckets];
+    int *h = hist + (int64_t)blockIdx.x * kCostBuckets;
+    const int t = threadIdx.x;  // blockDim.x == kCostBuckets
+    part[t] = h[t];
+    __syncthreads();
+    for (int d = 1; d < kCostBuckets; d <<= 1) {
+        const int v = t >= d ? part[t - d] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    h[t] = gbase[blockIdx.x] + part[t] - h[t];
+}
+
+// One thread per group: its place in decreasing cost order (groups of one
+// bucket in the order they claim it).
+__global__ void group_cost_scatter_kernel(const int *__restrict__ gbase, int n_ord, int total_groups,
+                                          const uint16_t *__restrict__ key, int *hist, int *gorder) {
+    for (int G = blockIdx.x * blockDim.x + threadIdx.x; G < total_groups; G += gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_ord - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (gbase[mid] <= G)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const int pos = atomicAdd(hist + (int64_t)lo * kCostBuckets + key[G], 1);
+        gorder[pos] = G - gbase[lo];
+    }
 }
 
 // Adaptive factoring (Banicescu and Liu's AF rule), the request half of
@@ -1192,6 +1335,23 @@ int blocks_per_sm_for(size_t smem_bytes, int modes) {
     else
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spin_kernel<false, kModeAll>, kThreads, smem_bytes);
     return e == cudaSuccess ? n : 0;
+}
+
+si_status enqueue_group_order(const ItemDesc *items, const int *ord_items, const int *gbase, int n_ord,
+                              int total_groups, uint16_t *key, int *hist, int *gorder, cudaStream_t st,
+                              int *kernels) {
+    *kernels = 0;
+    if (n_ord <= 0 || total_groups <= 0) return SI_OK;
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * (size_t)n_ord * kCostBuckets, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(cost histogram)");
+    const int warp_blocks = (int)std::min<int64_t>(((int64_t)total_groups + 7) / 8, 65535);
+    group_cost_kernel<<<warp_blocks, 256, 0, st>>>(items, ord_items, gbase, n_ord, total_groups, key, hist);
+    group_cost_scan_kernel<<<n_ord, kCostBuckets, 0, st>>>(gbase, hist);
+    const int blocks = (int)std::min<int64_t>(((int64_t)total_groups + 255) / 256, 65535);
+    group_cost_scatter_kernel<<<blocks, 256, 0, st>>>(gbase, n_ord, total_groups, key, hist, gorder);
+    *kernels = 3;
+    e = cudaGetLastError();
+    return e == cudaSuccess ? SI_OK : cuda_fail(e, "group cost order");
 }
 
 void launch_spin_kernel(const LaunchArgs &a, int blocks, size_t smem, cudaStream_t stream) {

@@ -104,7 +104,8 @@ si_status si_tune_mesh(si_mesh_t mesh, const int32_t *query_idx, int64_t m, int3
                 cur = s;
             }
         }
-    // stage 2: loop rule x minimum chunk x worker count
+    // stage 2: loop rule x minimum chunk x worker count x group order (the
+    // dynamic rules in grid order and in decreasing estimated cost)
     const int l2 = choose_log2_group(W, cur.group);
     const size_t smem = spin_smem_bytes(W, l2);
     const int per_sm = std::max(1, blocks_per_sm_for(smem, ring_mode(l2)));
@@ -113,17 +114,19 @@ si_status si_tune_mesh(si_mesh_t mesh, const int32_t *query_idx, int64_t m, int3
     for (int kind = SI_SCHED_STATIC; kind <= SI_SCHED_FAC; ++kind)
         for (int mc : {1, 2, 4}) {
             if (kind == SI_SCHED_STATIC && mc != 1) continue;
-            for (int w : worker_opts) {
-                si_schedule s{kind, mc, w, cur.group, cur.grid_div};
-                double ms;
-                si_status r =
-                    time_one(mesh, query_idx, m, W, bin_size, cos_support_angle, s, scratch_out, reps, st, &ms);
-                if (r != SI_OK) return r;
-                if (ms < cur_ms) {
-                    cur_ms = ms;
-                    cur = s;
+            for (int w : worker_opts)
+                for (int order = 0; order <= (kind == SI_SCHED_STATIC ? 0 : 1); ++order) {
+                    si_schedule s{kind, mc, w, cur.group, cur.grid_div};
+                    s.order = order;
+                    double ms;
+                    si_status r =
+                        time_one(mesh, query_idx, m, W, bin_size, cos_support_angle, s, scratch_out, reps, st, &ms);
+                    if (r != SI_OK) return r;
+                    if (ms < cur_ms) {
+                        cur_ms = ms;
+                        cur = s;
+                    }
                 }
-            }
         }
     *best = cur;
     if (best_ms) *best_ms = cur_ms;
@@ -177,9 +180,9 @@ si_status si_tune_save(const char *path) {
         const si_schedule &s = e.second.s;
         std::fprintf(f,
                      "  {\"W\": %d, \"log2n\": %d, \"log2m\": %d, \"kind\": %d, \"min_chunk\": %d, "
-                     "\"num_workers\": %d, \"group\": %d, \"grid_div\": %d, \"ms\": %.6f}%s\n",
+                     "\"num_workers\": %d, \"group\": %d, \"grid_div\": %d, \"order\": %d, \"ms\": %.6f}%s\n",
                      std::get<0>(e.first), std::get<1>(e.first), std::get<2>(e.first), s.kind, s.min_chunk,
-                     s.num_workers, s.group, s.grid_div, e.second.ms, ++k < g_table.size() ? "," : "");
+                     s.num_workers, s.group, s.grid_div, s.order, e.second.ms, ++k < g_table.size() ? "," : "");
     }
     std::fprintf(f, "]}\n");
     std::fclose(f);
@@ -187,7 +190,7 @@ si_status si_tune_save(const char *path) {
 }
 
 // Reads the format written by si_tune_save: one object per entry with the
-// nine numeric fields in any order.
+// nine numeric fields in any order, and "order" (0 when absent).
 si_status si_tune_load(const char *path) {
     if (!path) {
         set_error("si_tune_load: NULL path");
@@ -225,8 +228,11 @@ si_status si_tune_load(const char *path) {
         if (field("W", &W) && field("log2n", &ln) && field("log2m", &lm) && field("kind", &kind) &&
             field("min_chunk", &mc) && field("num_workers", &nw) && field("group", &g) && field("grid_div", &d)) {
             if (!field("ms", &ms)) ms = 0;
+            double ord = 0;
+            if (!field("order", &ord)) ord = 0;  // tables written before the field existed
             si_schedule s{(int)kind, (int)mc, (int)nw, (int)g, (int)d};
-            if (s.kind < 0 || s.kind > 3 || s.grid_div < 0 || s.grid_div > 16) {
+            s.order = (int)ord;
+            if (s.kind < 0 || s.kind > 3 || s.grid_div < 0 || s.grid_div > 16 || s.order < 0 || s.order > 1) {
                 set_error("si_tune_load: bad entry in %s", path);
                 return SI_ERR_INVALID;
             }

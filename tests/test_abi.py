@@ -114,16 +114,16 @@ def test_tuning_table_json_round_trip(lib, tmp_path):
     path = tmp_path / "t.json"
     path.write_text(json.dumps({"entries": [
         {"W": 32, "log2n": 16, "log2m": 16, "kind": 3, "min_chunk": 2, "num_workers": 0, "group": 16,
-         "grid_div": 8, "ms": 8.5},
+         "grid_div": 8, "order": 1, "ms": 8.5},
         {"W": 16, "log2n": 12, "log2m": 12, "kind": 1, "min_chunk": 1, "num_workers": 304, "group": 32,
          "grid_div": 4, "ms": 0.3}]}))
     spin.si_tune_load(str(path))
     s = spin.si_tune_lookup(32, 100_000, 100_000)  # log2 = 16: exact class
-    assert (s.kind, s.min_chunk, s.group, s.grid_div) == (3, 2, 16, 8)
+    assert (s.kind, s.min_chunk, s.group, s.grid_div, s.order) == (3, 2, 16, 8, 1)
     s = spin.si_tune_lookup(32, 150_000, 40_000)  # nearest class with the same W
     assert s.kind == 3
     s = spin.si_tune_lookup(16, 4096, 4096)
-    assert (s.kind, s.num_workers, s.group) == (1, 304, 32)
+    assert (s.kind, s.num_workers, s.group, s.order) == (1, 304, 32, 0)  # no "order": grid order
     assert spin.si_tune_lookup(64, 4096, 4096) is None  # no entry for W = 64
     out = tmp_path / "u.json"
     spin.si_tune_save(str(out))
@@ -133,6 +133,7 @@ def test_tuning_table_json_round_trip(lib, tmp_path):
     assert spin.si_tune_lookup(32, 100_000, 100_000) is None
     spin.si_tune_load(str(out))
     assert spin.si_tune_lookup(32, 100_000, 100_000).grid_div == 8
+    assert spin.si_tune_lookup(32, 100_000, 100_000).order == 1
     spin.si_tune_clear()
     bad = tmp_path / "bad.json"
     bad.write_text('{"entries": [{"W": 8, "log2n": 1, "log2m": 1, "kind": 9, "min_chunk": 1, '
