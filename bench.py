@@ -420,6 +420,9 @@ def run_ours(args):
         P = spin.si_default_workers(c["W"], spin.make_schedule("FAC", **shape))
         het = {k: spin.make_schedule(k, num_workers=P, slow_workers=P // 2, slowdown=3.0, fac_cov=cov, **shape)
                for k in ("STATIC", "SS", "GSS", "FAC", "FAC_PROB", "AWF", "AF")}
+        for k in ("FAC", "AWF"):
+            het[k + "+cost order"] = spin.make_schedule(k, num_workers=P, slow_workers=P // 2, slowdown=3.0,
+                                                        order=1, **shape)
         h = bench_single(spin, torch, dev, c, ex_steps, args.warmup, flush, stream, scheds=het)
         h["emulation"] = {"workers": P, "slow_workers": P // 2, "slowdown": 3.0, "slow_request_first": True}
         h["over_static"] = {k: v["images_per_s"] / h["by_schedule"]["STATIC"]["images_per_s"]
@@ -563,8 +566,9 @@ def bench_trace(spin, torch, dev, c, shape, stream, het=None):
     mesh = spin.si_mesh_create(tp, tn, n, stream)
     res = {}
     try:
-        for kind in ("STATIC", "SS", "GSS", "FAC", "AWF", "AF"):
-            sched = spin.make_schedule(kind, **shape, **(het or {}))
+        for name in ("STATIC", "SS", "GSS", "FAC", "AWF", "AF", "FAC+cost order", "AWF+cost order"):
+            kind = name.split("+")[0]
+            sched = spin.make_schedule(kind, order=1 if "+" in name else 0, **shape, **(het or {}))
             P = spin.si_default_workers(W, sched) if not het else het["num_workers"]
             claims = torch.zeros((200000, 4), dtype=torch.int64, device=dev)
             count = torch.zeros(1, dtype=torch.int64, device=dev)
@@ -579,7 +583,7 @@ def bench_trace(spin, torch, dev, c, shape, stream, het=None):
             for w, _, a, b in tr:
                 finish[w] = max(finish[w], (b - t0) / 1e6)
                 busy[w] += (b - a) / 1e6
-            res[kind] = {"claims": nc, "workers": int(P), "finish_ms_max": float(finish.max()),
+            res[name] = {"claims": nc, "workers": int(P), "finish_ms_max": float(finish.max()),
                          "finish_ms_mean": float(finish.mean()), "finish_ms_min": float(finish.min()),
                          "finish_quartiles_ms": _quartiles(finish),
                          "imbalance": float((finish.max() - finish.mean()) / finish.max()),
