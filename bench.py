@@ -274,7 +274,7 @@ def run_ours(args):
     # launch shape from the autotuner (untimed): group size and grid resolution
     # are shared by every rule below; "tuned" is the tuner's full choice
     mesh = spin.si_mesh_create(tp, tn, n, stream)
-    tuned, tuned_ms = spin.si_tune_mesh(mesh, None, m, W, B, cs, out, reps=2, stream=stream)
+    tuned, tuned_ms = spin.si_tune_mesh(mesh, None, m, W, B, cs, out, reps=3, stream=stream)
     spin.si_mesh_destroy(mesh)
     shape = dict(group=tuned.group, grid_div=tuned.grid_div)
     configs = {name: spin.make_schedule(name, **shape) for name in SCHEDULES}

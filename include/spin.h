@@ -138,8 +138,11 @@ typedef struct si_schedule {
                             (the loop as written); 1 -> decreasing estimated cost (the number of
                             candidates in each group's grid stencil, bucketed by 2^(1/32)), so
                             the cheapest groups come last and the last chunks balance the
-                            workers' finishing times.  The estimate costs three small kernels per
-                            call.  Results are unchanged.  STATIC always runs grid order. */
+                            workers' finishing times.  Within a run of equal chunks of the
+                            rule's table (a FAC batch) the sorted groups are dealt round-robin
+                            over the chunks, so that no chunk bundles the costliest ones.  The
+                            estimate costs three small kernels per call.  Results are unchanged.
+                            STATIC always runs grid order. */
 } si_schedule;
 
 /* Optional per-image probes (device buffers of m entries, each may be NULL).

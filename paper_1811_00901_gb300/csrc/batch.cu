@@ -123,9 +123,9 @@ struct Plan {
     // adaptive rules (AWF, AF): unit bases of the items; af: the rule is AF
     bool awf = false;
     bool af = false;
-    // cost order (si_schedule.order = 1): the ordered items and their first
-    // group in the concatenated group space
-    std::vector<int> ord;  // ord_items, then gbase[n_ord + 1]
+    // cost order (si_schedule.order = 1): the ordered items, their first group
+    // in the concatenated group space and their deal batches
+    std::vector<int> ord;  // ord_items[n_ord], gbase[n_ord + 1], dbase[n_ord + 1], deal[3 x batches]
     int n_ord = 0, ord_groups = 0;
     int awf_min_chunk = 1;
     std::vector<int> awf_ubase;
@@ -254,6 +254,7 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
     p->af = n_af > 0;
     n_awf += n_af;
     p->step_piece.assign(1, 0);
+    std::vector<std::vector<int64_t>> tables(nitems);  // each item's chunk table (dynamic rules)
     if (n_awf > 0) {
         // one loop over the concatenated units, chunk sizes decided on the device
         p->awf = true;
@@ -296,6 +297,7 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
         for (int k : order) {
             if (p->units[k] == 0) continue;
             chunk_table(scheds[k].kind, p->units[k], workers, scheds[k].min_chunk, scheds[k].fac_cov, &st);
+            tables[k] = st;
             for (size_t s = 0; s + 1 < st.size(); ++s) {
                 if (st[s + 1] == st[s]) continue;
                 p->pieces.push_back(Piece{k, (int)st[s], (int)st[s + 1], 0});
@@ -305,9 +307,13 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
     }
     if (!p->awf) p->nsteps = (int)p->step_piece.size() - 1;
 
-    // ---- cost order of the groups of the dynamic rules' items that ask for it
+    // ---- cost order of the groups of the dynamic rules' items that ask for it.
+    // Deal batches: within a run of equal chunks of the item's table (a FAC
+    // batch), the cost-sorted groups are dealt round-robin over the run's
+    // chunks, so that no chunk bundles the costliest groups (a chunk of c
+    // groups from the top of the order could outlast a worker's whole share)
     {
-        std::vector<int> oi, gb(1, 0);
+        std::vector<int> oi, gb(1, 0), db(1, 0), deal;
         for (int k = 0; k < nitems; ++k) {
             if (items[k].m == 0 || scheds[k].order != 1 || scheds[k].kind == SI_SCHED_STATIC || p->all_static)
                 continue;
@@ -315,11 +321,32 @@ si_status plan_batch(const std::vector<si_batch_item> &items, const std::vector<
             if (groups < 2) continue;
             oi.push_back(k);
             gb.push_back(gb.back() + groups);
+            const std::vector<int64_t> &t = tables[k];
+            if (p->slices[k] == 1 && t.size() > 2) {
+                size_t s = 0;
+                while (s + 1 < t.size()) {
+                    const int64_t c = t[s + 1] - t[s];
+                    size_t e = s + 1;
+                    while (e + 1 < t.size() && t[e + 1] - t[e] == c && (int64_t)(e - s) < workers) ++e;
+                    const int64_t nc = (int64_t)(e - s);
+                    if (c >= 2 && nc >= 2) {
+                        deal.push_back((int)t[s]);
+                        deal.push_back((int)nc);
+                        deal.push_back((int)c);
+                    }
+                    s = e;
+                }
+            }
+            db.push_back((int)deal.size() / 3);
         }
         p->n_ord = (int)oi.size();
         p->ord_groups = gb.back();
         p->ord = oi;
-        if (p->n_ord > 0) p->ord.insert(p->ord.end(), gb.begin(), gb.end());
+        if (p->n_ord > 0) {
+            p->ord.insert(p->ord.end(), gb.begin(), gb.end());
+            p->ord.insert(p->ord.end(), db.begin(), db.end());
+            p->ord.insert(p->ord.end(), deal.begin(), deal.end());
+        }
     }
 
     // ---- query sorting (items that are not "all points of the mesh")
@@ -490,7 +517,8 @@ si_status record_batch(const Plan &p, const std::vector<si_batch_item> &items, c
         const int *d_ord = reinterpret_cast<const int *>(scratch + p.o_ord);
         int kk = 0;
         si_status st = enqueue_group_order(reinterpret_cast<const ItemDesc *>(scratch + p.o_items), d_ord,
-                                           d_ord + p.n_ord, p.n_ord, p.ord_groups,
+                                           d_ord + p.n_ord, d_ord + 2 * p.n_ord + 1, d_ord + 3 * p.n_ord + 2,
+                                           p.n_ord, p.ord_groups,
                                            reinterpret_cast<uint16_t *>(scratch + p.o_gkey),
                                            reinterpret_cast<int *>(scratch + p.o_ghist),
                                            reinterpret_cast<int *>(scratch + p.o_gorder), stream, &kk);

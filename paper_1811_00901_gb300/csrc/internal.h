@@ -148,13 +148,17 @@ struct ItemDesc {
 // ord_items[0..n_ord) of a launch, whose groups occupy [gbase[j], gbase[j+1])
 // of a concatenated group space, estimate each group's cost (the candidates
 // of its stencil), bucket it by log cost and write each item's groups in
-// decreasing bucket order to gorder[gbase[j] ..].  Scratch: key[gbase[n_ord]]
-// and hist[n_ord * kCostBuckets].  Four stream-ordered operations (a memset
-// and three kernels); returns the kernels launched in *kernels.
+// decreasing bucket order to gorder[gbase[j] ..].  Item j's deal batches,
+// deal[3b .. 3b+2] = (first position, chunks nc, chunk size c) for b in
+// [dbase[j], dbase[j+1]), spread the positions of such a run of equal chunks
+// round-robin: sorted rank start + i goes to chunk i mod nc, slot i div nc.
+// Scratch: key[gbase[n_ord]] and hist[n_ord * kCostBuckets].  Four
+// stream-ordered operations (a memset and three kernels); returns the
+// kernels launched in *kernels.
 constexpr int kCostBuckets = 1024;
-si_status enqueue_group_order(const ItemDesc *items, const int *ord_items, const int *gbase, int n_ord,
-                              int total_groups, uint16_t *key, int *hist, int *gorder, cudaStream_t st,
-                              int *kernels);
+si_status enqueue_group_order(const ItemDesc *items, const int *ord_items, const int *gbase, const int *dbase,
+                              const int *deal, int n_ord, int total_groups, uint16_t *key, int *hist, int *gorder,
+                              cudaStream_t st, int *kernels);
 
 // A piece of the scheduled loop: units [u0, u1) of item `item`.
 struct Piece {
@@ -240,6 +244,7 @@ inline int launch_modes_for(int modes, size_t smem_bytes, bool probe) {
 si_status mesh_create(const float *points, const float *normals, int64_t n, si_stream stream, si_mesh_t *out_mesh,
                       bool check_host);
 Grid *mesh_grid(Mesh *m, float cell, cudaStream_t stream, si_status *st);
+void mesh_drop_grids(Mesh *m);
 // Cells a grid of a mesh of n points may have (the coarsening bound).
 int64_t grid_cell_cap(int64_t n);
 // Candidate threshold of a binning: fl32(R^2 (1 + 1e-5)) with R^2 = h^2 +

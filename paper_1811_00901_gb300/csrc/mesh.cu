@@ -220,6 +220,17 @@ float grid_cell_for(const Mesh *m, int W, float bin, int grid_div) {
     return (float)std::exp2(e);
 }
 
+// Drops the mesh's grids; the next call that needs one builds it again.  The
+// cached batch graphs that hold the grids' pointers go first, then the device
+// finishes its work, as in si_mesh_destroy.
+void mesh_drop_grids(Mesh *m) {
+    forget_mesh_graphs(m);
+    std::lock_guard<std::mutex> lk(m->mu);
+    cudaDeviceSynchronize();
+    for (Grid *g : m->grids) free_grid(g, nullptr);
+    m->grids.clear();
+}
+
 Grid *mesh_grid(Mesh *m, float cell, cudaStream_t stream, si_status *st) {
     *st = SI_OK;
     std::lock_guard<std::mutex> lk(m->mu);

@@ -975,9 +975,11 @@ __global__ void group_cost_scan_kernel(const int *__restrict__ gbase, int *hist)
     h[t] = gbase[blockIdx.x] + part[t] - h[t];
 }
 
-// One thread per group: its place in decreasing cost order (groups of one
-// bucket in the order they claim it).
-__global__ void group_cost_scatter_kernel(const int *__restrict__ gbase, int n_ord, int total_groups,
+// One thread per group: its rank in decreasing cost order (groups of one
+// bucket in the order they claim it), dealt over the chunks of its deal
+// batch, gives its loop position.
+__global__ void group_cost_scatter_kernel(const int *__restrict__ gbase, const int *__restrict__ dbase,
+                                          const int *__restrict__ deal, int n_ord, int total_groups,
                                           const uint16_t *__restrict__ key, int *hist, int *gorder) {
     for (int G = blockIdx.x * blockDim.x + threadIdx.x; G < total_groups; G += gridDim.x * blockDim.x) {
         int lo = 0, hi = n_ord - 1;
@@ -988,8 +990,17 @@ __global__ void group_cost_scatter_kernel(const int *__restrict__ gbase, int n_o
             else
                 hi = mid - 1;
         }
-        const int pos = atomicAdd(hist + (int64_t)lo * kCostBuckets + key[G], 1);
-        gorder[pos] = G - gbase[lo];
+        const int r = atomicAdd(hist + (int64_t)lo * kCostBuckets + key[G], 1) - gbase[lo];
+        int pos = r;
+        for (int b = dbase[lo]; b < dbase[lo + 1]; ++b) {
+            const int s0 = deal[3 * b], nc = deal[3 * b + 1], c = deal[3 * b + 2];
+            if (r >= s0 && r - s0 < nc * c) {
+                const int off = r - s0;
+                pos = s0 + (off % nc) * c + off / nc;
+                break;
+            }
+        }
+        gorder[gbase[lo] + pos] = G - gbase[lo];
     }
 }
 
@@ -1337,9 +1348,9 @@ int blocks_per_sm_for(size_t smem_bytes, int modes) {
     return e == cudaSuccess ? n : 0;
 }
 
-si_status enqueue_group_order(const ItemDesc *items, const int *ord_items, const int *gbase, int n_ord,
-                              int total_groups, uint16_t *key, int *hist, int *gorder, cudaStream_t st,
-                              int *kernels) {
+si_status enqueue_group_order(const ItemDesc *items, const int *ord_items, const int *gbase, const int *dbase,
+                              const int *deal, int n_ord, int total_groups, uint16_t *key, int *hist, int *gorder,
+                              cudaStream_t st, int *kernels) {
     *kernels = 0;
     if (n_ord <= 0 || total_groups <= 0) return SI_OK;
     cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * (size_t)n_ord * kCostBuckets, st);
@@ -1348,7 +1359,7 @@ si_status enqueue_group_order(const ItemDesc *items, const int *ord_items, const
     group_cost_kernel<<<warp_blocks, 256, 0, st>>>(items, ord_items, gbase, n_ord, total_groups, key, hist);
     group_cost_scan_kernel<<<n_ord, kCostBuckets, 0, st>>>(gbase, hist);
     const int blocks = (int)std::min<int64_t>(((int64_t)total_groups + 255) / 256, 65535);
-    group_cost_scatter_kernel<<<blocks, 256, 0, st>>>(gbase, n_ord, total_groups, key, hist, gorder);
+    group_cost_scatter_kernel<<<blocks, 256, 0, st>>>(gbase, dbase, deal, n_ord, total_groups, key, hist, gorder);
     *kernels = 3;
     e = cudaGetLastError();
     return e == cudaSuccess ? SI_OK : cuda_fail(e, "group cost order");

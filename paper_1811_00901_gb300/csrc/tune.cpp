@@ -47,6 +47,14 @@ si_status time_one(si_mesh_t mesh, const int32_t *q, int64_t m, int W, float B, 
     si_status r = si_generate(mesh, q, m, W, B, c, s, out, (si_stream)st);
     std::vector<double> t;
     for (int k = 0; r == SI_OK && k < reps; ++k) {
+        // each repetition on a freshly built grid (untimed): a grid's order of
+        // points within a cell comes from atomics, so rebuilding changes which
+        // points share a group, and with it how a rule's chunks balance (most
+        // for the cost order, whose first chunks hold the costliest groups);
+        // the median then stands for a new mesh, not for one lucky build
+        mesh_drop_grids(reinterpret_cast<Mesh *>(mesh));
+        r = si_mesh_prepare(mesh, W, B, &s, (si_stream)st);
+        if (r != SI_OK) break;
         cudaEventRecord(e0, st);
         r = si_generate(mesh, q, m, W, B, c, s, out, (si_stream)st);
         cudaEventRecord(e1, st);
@@ -115,7 +123,10 @@ si_status si_tune_mesh(si_mesh_t mesh, const int32_t *query_idx, int64_t m, int3
         for (int mc : {1, 2, 4}) {
             if (kind == SI_SCHED_STATIC && mc != 1) continue;
             for (int w : worker_opts)
-                for (int order = 0; order <= (kind == SI_SCHED_STATIC ? 0 : 1); ++order) {
+                // (GSS's chunks shrink with the remaining work: its runs of equal chunks
+                // to deal the costliest groups over are short, and its first chunks are
+                // its largest, so it stays in grid order)
+                for (int order = 0; order <= (kind == SI_SCHED_STATIC || kind == SI_SCHED_GSS ? 0 : 1); ++order) {
                     si_schedule s{kind, mc, w, cur.group, cur.grid_div};
                     s.order = order;
                     double ms;

@@ -114,3 +114,43 @@ def test_batched_items_in_cost_order():
     finally:
         for mh in meshes:
             spin.si_mesh_destroy(mh)
+
+
+def test_fac_batches_deal_the_costliest_groups():
+    """FAC in cost order: within each batch of equal chunks the cost-sorted
+    groups are dealt round-robin, so the chunks of the first batch (the
+    costliest groups) carry nearly equal work, and the batches' groups get
+    cheaper along the loop.  Every image still comes from exactly one claim."""
+    import torch
+
+    import paper_1811_00901_gb300 as spin
+    pts, nrm = wl.heightfield(20_000, 93)
+    W, B, c = 32, 0.01, wl.cos_deg(60.0)
+    group, P, m = 8, 64, 20_000
+    dev = torch.device("cuda:0")
+    mesh = spin.si_mesh_create(torch.from_numpy(pts).to(dev), torch.from_numpy(nrm).to(dev))
+    try:
+        out = torch.empty((m, W, W), dtype=torch.int32, device=dev)
+        step = torch.full((m,), -1, dtype=torch.int32, device=dev)
+        examined = torch.full((m,), -1, dtype=torch.int64, device=dev)
+        sched = spin.make_schedule("FAC", group=group, num_workers=P, order=1)
+        spin.si_generate_probe(mesh, None, m, W, B, c, sched, out, step=step, examined=examined)
+        torch.cuda.synchronize()
+        spin.si_get_stats(mesh)
+        step, examined = step.cpu().numpy(), examined.cpu().numpy()
+    finally:
+        spin.si_mesh_destroy(mesh)
+    from oracle import dls
+    groups = -(-m // group)
+    starts = dls.chunk_starts(dls.FAC, groups, P, 1)
+    assert (step >= 0).all() and step.max() == len(starts) - 2
+    per_step_images = np.bincount(step, minlength=len(starts) - 1)
+    sizes = np.diff(starts)
+    np.testing.assert_array_equal(per_step_images[:-1], sizes[:-1] * group)  # the table's chunks, whole groups
+    work = np.bincount(step, weights=examined.astype(np.float64), minlength=len(starts) - 1)  # pairs per claim
+    first = work[:P]
+    assert sizes[0] >= 10 and (sizes[:P] == sizes[0]).all()
+    assert first.max() <= 1.25 * first.min(), (first.min(), first.max())
+    per_group = work / (sizes * group)
+    last_batch = per_group[len(sizes) - P:]
+    assert per_group[:P].mean() > 1.2 * last_batch.mean()
