@@ -420,7 +420,7 @@ def run_ours(args):
         P = spin.si_default_workers(c["W"], spin.make_schedule("FAC", **shape))
         het = {k: spin.make_schedule(k, num_workers=P, slow_workers=P // 2, slowdown=3.0, fac_cov=cov, **shape)
                for k in ("STATIC", "SS", "GSS", "FAC", "FAC_PROB", "AWF", "AF")}
-        for k in ("FAC", "AWF"):
+        for k in ("SS", "FAC", "AWF"):
             het[k + "+cost order"] = spin.make_schedule(k, num_workers=P, slow_workers=P // 2, slowdown=3.0,
                                                         order=1, **shape)
         h = bench_single(spin, torch, dev, c, ex_steps, args.warmup, flush, stream, scheds=het)
@@ -566,7 +566,7 @@ def bench_trace(spin, torch, dev, c, shape, stream, het=None):
     mesh = spin.si_mesh_create(tp, tn, n, stream)
     res = {}
     try:
-        for name in ("STATIC", "SS", "GSS", "FAC", "AWF", "AF", "FAC+cost order", "AWF+cost order"):
+        for name in ("STATIC", "SS", "GSS", "FAC", "AWF", "AF", "SS+cost order", "FAC+cost order", "AWF+cost order"):
             kind = name.split("+")[0]
             sched = spin.make_schedule(kind, order=1 if "+" in name else 0, **shape, **(het or {}))
             P = spin.si_default_workers(W, sched) if not het else het["num_workers"]
