@@ -340,9 +340,12 @@ si_status si_reset_stats(si_mesh_t mesh);
 void si_set_timing(int32_t enabled);
 
 /* --------------------------------------------------------------- tuning --
- * The autotuner times candidate (rule, min_chunk, workers, group, grid_div)
- * settings on a mesh and records the fastest per size class (W, log2 of the
- * point count, log2 of the image count).  si_generate_batched consults it. */
+ * The autotuner times candidate (rule, min_chunk, workers, group, grid_div,
+ * order) settings on a mesh and records the fastest per size class (W, log2
+ * of the point count, log2 of the image count).  si_generate_batched consults
+ * it.  Each timed repetition runs on a freshly built grid: the tuner drops the
+ * mesh's grids (after synchronizing the device) and builds them again, so the
+ * mesh must not be in use on another stream or thread during the call. */
 si_status si_tune_mesh(si_mesh_t mesh, const int32_t *query_idx, int64_t m, int32_t W,
                        float bin_size, float cos_support_angle, int32_t *scratch_out,
                        int32_t reps, si_schedule *best, double *best_ms, si_stream stream);
