@@ -31,6 +31,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 #include <mutex>
@@ -189,7 +190,8 @@ template <int L>
 __global__ void __launch_bounds__(kTcThreads, 1)
     match_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                     const int n_scene, const int n_model, const int k_slices, const int tiles, const int parts,
-                    const int k, float *__restrict__ part_v, int *__restrict__ part_i, unsigned *err) {
+                    const int band_m, const int k, float *__restrict__ part_v, int *__restrict__ part_i,
+                    unsigned *err) {
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = smem_addr(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;  // 128-byte swizzle atoms need 1024-byte alignment
@@ -197,10 +199,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     TcBarriers &B = *reinterpret_cast<TcBarriers *>(sbase + kStagesTc * kStageBytes);
     volatile int *abort_flag = &B.abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // part-major order: the CTAs resident at one time work on the same model
-    // range, so its tiles come from DRAM once and from L2 after that
+    // banded part-major order: the scene blocks are taken in bands of band_m,
+    // and within a band the CTAs run part by part, so the CTAs resident at one
+    // time share a model range (its tiles come from DRAM once, then from L2)
+    // and hold at most a band's scene operands, which stay in L2 while the
+    // band's parts stream past them
     const int mblocks = (n_scene + kBM - 1) / kBM;
-    const int part = blockIdx.x / mblocks, mb = blockIdx.x - part * mblocks;
+    const int full_bands = mblocks / band_m, per_band = band_m * parts;
+    int band = blockIdx.x / per_band, bm_eff = band_m;
+    if (band >= full_bands) {
+        band = full_bands;
+        bm_eff = mblocks - full_bands * band_m;
+    }
+    const int idx = blockIdx.x - band * per_band;
+    const int part = idx / bm_eff, mb = band * band_m + (idx - (idx / bm_eff) * bm_eff);
     const int t0 = (int)((int64_t)tiles * part / parts), t1 = (int)((int64_t)tiles * (part + 1) / parts);
     const int ntile = t1 - t0;
 
@@ -496,8 +508,12 @@ si_status match_tc_launch(const __nv_bfloat16 *a, int64_t n_scene, const __nv_bf
     const int64_t mblocks = (n_scene + kBM - 1) / kBM;
     const int tiles = (int)((n_model + kBN - 1) / kBN);
     auto kern = k <= 8 ? match_tc_kernel<8> : match_tc_kernel<kMatchTcMaxK>;
+    // scene blocks per band: as many as leave L2 (129 MB) room for the model
+    // stream, about 48 MB of scene operands (all blocks in BF16 mode at W <= 64)
+    const int64_t a_block_bytes = (int64_t)kBM * kp * 2;
+    const int band_m = (int)std::max<int64_t>(1, std::min<int64_t>(mblocks, (48ll << 20) / a_block_bytes));
     kern<<<(unsigned)(mblocks * parts), kTcThreads, kTcSmem, st>>>(ma, mbm, (int)n_scene, (int)n_model, kp / kBK,
-                                                                  tiles, parts, k, part_v, part_i, err);
+                                                                  tiles, parts, band_m, k, part_v, part_i, err);
     note_launches(1);
     SI_CUDA(cudaGetLastError());
     // two lists per row and part: one per column half of the tiles
