@@ -154,3 +154,19 @@ def test_fac_batches_deal_the_costliest_groups():
     per_group = work / (sizes * group)
     last_batch = per_group[len(sizes) - P:]
     assert per_group[:P].mean() > 1.2 * last_batch.mean()
+
+
+def test_cost_order_from_host_buffers():
+    """si_generate_host (host points, normals and output; mesh and grid built
+    inside the call) in cost order gives the device path's images."""
+    import torch
+
+    import paper_1811_00901_gb300 as spin
+    pts, nrm = wl.heightfield(8000, 94)
+    W, B, c = 32, 0.01, wl.cos_deg(60.0)
+    ref, _ = gpu_run(pts, nrm, W, B, c, schedule=spin.make_schedule("STATIC"))
+    out = torch.empty((8000, W, W), dtype=torch.int32).pin_memory()
+    spin.si_generate_host(torch.from_numpy(pts), torch.from_numpy(nrm), 8000, None, 8000, W, B, c,
+                          spin.make_schedule("FAC", order=1), out)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.numpy(), ref)

@@ -143,5 +143,10 @@ def test_no_alloc_rejects_what_it_cannot_do_without_allocating():
             spin.si_generate_noalloc(mesh, None, 3000, 16, 0.05, 0.5, spin.make_schedule("GSS", slices=2), out)
         assert e.value.status == spin.SI_ERR_INVALID
         assert "slice" in spin.si_last_error()
+        # the cost order needs scratch for its estimate and its sort: refused
+        with pytest.raises(spin.SpinError) as e:
+            spin.si_generate_noalloc(mesh, None, 3000, 16, 0.05, 0.5, spin.make_schedule("FAC", order=1), out)
+        assert e.value.status == spin.SI_ERR_INVALID
+        assert "order" in spin.si_last_error()
     finally:
         spin.si_mesh_destroy(mesh)
