@@ -203,13 +203,13 @@ def _ncu_traffic(workload):
 #   per contributing pair: fraction split (2), product weight (2), the other
 #   weights (3), row and column of the address (4), four shared-memory int32
 #   atomics (4), count (1)                                              -> 16
-# The survey's per-unit estimates (8 per culled pair, ~30 per angle-passing
-# pair, 4 read-modify-writes + ~6 integer ops per in-support pair) give the
-# second figure, roofline["survey_counts"].
+# A coarser per-unit estimate (8 per culled pair, ~30 per angle-passing pair,
+# 4 read-modify-writes + ~6 integer ops per in-support pair) gives a second
+# figure, roofline["coarse_counts"].
 OPS_PER_CULLED = 7
 OPS_PER_ANGLE = 15
 OPS_PER_SUPPORT = 16
-SURVEY_OPS = (8, 30, 10)
+COARSE_OPS = (8, 30, 10)
 
 
 def alu_ops(n_culled, n_angle, n_support, counts=(OPS_PER_CULLED, OPS_PER_ANGLE, OPS_PER_SUPPORT)):
@@ -362,15 +362,15 @@ def run_ours(args):
     ops = alu_ops(n_culled, n_angle, n_support)
     k_ms = kernel_ms[best]
     achieved = ops / (k_ms / 1e3)
-    achieved_s = alu_ops(n_culled, n_angle, n_support, SURVEY_OPS) / (k_ms / 1e3)
+    achieved_s = alu_ops(n_culled, n_angle, n_support, COARSE_OPS) / (k_ms / 1e3)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12, "unit": "Tlane-op/s",
                 "frac": achieved / alu_peak, "traffic": _ncu_traffic(c["name"]),
                 "kernel": "spin_kernel (persistent, %s)" % best, "kernel_ms": k_ms,
                 "peak_source": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)" % (sms, f_mhz, peak_src),
                 "ops_per_culled_pair": OPS_PER_CULLED, "ops_per_angle_pair": OPS_PER_ANGLE,
                 "ops_per_support_pair": OPS_PER_SUPPORT,
-                "survey_counts": {"ops_per_culled_pair": SURVEY_OPS[0], "ops_per_angle_pair": SURVEY_OPS[1],
-                                  "ops_per_support_pair": SURVEY_OPS[2], "achieved": achieved_s / 1e12,
+                "coarse_counts": {"ops_per_culled_pair": COARSE_OPS[0], "ops_per_angle_pair": COARSE_OPS[1],
+                                  "ops_per_support_pair": COARSE_OPS[2], "achieved": achieved_s / 1e12,
                                   "frac": achieved_s / alu_peak},
                 "peak_at_clocks": {"%.0f_mhz" % f: {"peak": sms * 128 * f * 1e6 / 1e12,
                                                     "frac": achieved / (sms * 128 * f * 1e6)}
@@ -522,8 +522,8 @@ def bench_single(spin, torch, dev, c, steps, warmup, flush, stream, kinds=("STAT
                     roofline={"bound": "alu", "unit": "Tlane-op/s", "rule": best, "kernel_ms": res[best]["kernel_ms"],
                               "achieved": alu_ops(nc, na, ns) / k_s / 1e12, "peak": alu_peak / 1e12,
                               "frac": alu_ops(nc, na, ns) / k_s / alu_peak,
-                              "survey_counts": {"achieved": alu_ops(nc, na, ns, SURVEY_OPS) / k_s / 1e12,
-                                                "frac": alu_ops(nc, na, ns, SURVEY_OPS) / k_s / alu_peak},
+                              "coarse_counts": {"achieved": alu_ops(nc, na, ns, COARSE_OPS) / k_s / 1e12,
+                                                "frac": alu_ops(nc, na, ns, COARSE_OPS) / k_s / alu_peak},
                               "peak_source": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)" % (
                                   sms_count(torch, dev), f_mhz, src),
                               "write_gbs": m * W * W * 4 / k_s / 1e9})
