@@ -120,7 +120,7 @@ typedef struct si_schedule {
     int32_t num_workers; /* persistent thread blocks P (0 -> all SMs x blocks per SM, the count
                             si_default_workers returns) */
     int32_t group;       /* images per group: 1, 2, 4, 8, 16 or 32 (0 -> by W) */
-    int32_t grid_div;    /* grid cells per candidate radius, 1..16 (0 -> 8) */
+    int32_t grid_div;    /* grid cells per candidate radius, 1..16 (0 -> 8, or 6 for W >= 64) */
     int32_t slices;      /* blocks that share one group's candidate stream, 1..64; each adds
                             its partial images into `out` with integer atomics (results are
                             unchanged).  0 -> auto: 1 when the call has enough groups to fill

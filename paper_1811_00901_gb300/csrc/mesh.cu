@@ -214,7 +214,7 @@ int64_t grid_cell_cap(int64_t n) { return std::min<int64_t>(int64_t(1) << 24, 8 
 float grid_cell_for(const Mesh *m, int W, float bin, int grid_div) {
     (void)m;
     double R = std::sqrt((double)si_candidate_rc2(W, bin));
-    int div = grid_div > 0 ? grid_div : 8;
+    int div = grid_div > 0 ? grid_div : (W >= 64 ? 6 : 8);  // measured defaults: wide images prefer coarser cells
     double c = R / div;
     double e = std::floor(std::log2(c) * 4.0) / 4.0;
     return (float)std::exp2(e);

@@ -400,7 +400,8 @@ constexpr bool has_full_path() {
 //  * all warps consuming (NCONS == kWarps): warp w takes trips at candidate
 //    w*cpw + 2*NCONS*cpw*t (a compile-time count, unrolled);
 //  * NCONS consumer warps: trip t covers candidates [2*cpw*t, 2*cpw*(t+1)),
-//    dealt round-robin.
+//    dealt round-robin (unrolled when every warp gets the same number of
+//    trips, which the producer-ring tile sizes are chosen for).
 template <int WT, int LS, bool PROBE, bool NB, int NCONS, int TN, bool FULL>
 __device__ __forceinline__ void consume_tile(const float4 *__restrict__ tile, const int len, const int warp,
                                              const int lane, const bool active, const float4 P, const float4 N,
@@ -422,9 +423,18 @@ __device__ __forceinline__ void consume_tile(const float4 *__restrict__ tile, co
         constexpr int kCpw = 32 >> LS;
         constexpr int kTrips = TN / (2 * kCpw);
         const float4 *t0 = tile + 2 * sub;
-        for (int tr = warp; tr < kTrips; tr += NCONS)
-            trip<WT, LS, PROBE, NB>(t0 + 4 * tr * kCpw, t0 + 4 * tr * kCpw + 2 * kCpw, active, active, P, N, k, sh,
-                                img_adj, cnt, pc_c, pc_s, pc_h);
+        if constexpr (kTrips % NCONS == 0) {
+#pragma unroll
+            for (int i = 0; i < kTrips / NCONS; ++i) {
+                const int tr = warp + i * NCONS;
+                trip<WT, LS, PROBE, NB>(t0 + 4 * tr * kCpw, t0 + 4 * tr * kCpw + 2 * kCpw, active, active, P, N, k,
+                                        sh, img_adj, cnt, pc_c, pc_s, pc_h);
+            }
+        } else {
+            for (int tr = warp; tr < kTrips; tr += NCONS)
+                trip<WT, LS, PROBE, NB>(t0 + 4 * tr * kCpw, t0 + 4 * tr * kCpw + 2 * kCpw, active, active, P, N, k,
+                                        sh, img_adj, cnt, pc_c, pc_s, pc_h);
+        }
     } else {
         for (int cb = warp * cpw; cb < len; cb += 2 * stride) {
             const int c0 = cb + sub, c1 = cb + stride + sub;

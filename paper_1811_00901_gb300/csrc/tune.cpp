@@ -98,7 +98,7 @@ si_status si_tune_mesh(si_mesh_t mesh, const int32_t *query_idx, int64_t m, int3
     // stage 1: group size x grid resolution under GSS
     std::vector<int> groups;
     for (int l = auto_l2; l >= 0 && l >= auto_l2 - 2; --l) groups.push_back(1 << l);
-    const int divs[] = {4, 8, 12};
+    const int divs[] = {4, 6, 8, 12};
     si_schedule cur{SI_SCHED_GSS, 1, 0, 1 << auto_l2, 4};
     double cur_ms = 1e30;
     for (int g : groups)
