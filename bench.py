@@ -402,8 +402,16 @@ def run_ours(args):
         from paper_1811_00901_gb300 import workloads as wl
         ex_steps = args.steps
         extra = {}
-        extra["sphere-4096-W16"] = bench_single(spin, torch, dev, wl.plain_sphere(), args.steps, args.warmup, flush,
-                                                stream, kinds=("STATIC", "SS", "GSS", "FAC"), pairs=True)
+        sph = wl.plain_sphere()
+        sph_tuned = _tuned_schedule(spin, torch, dev, sph, stream)
+        extra["sphere-4096-W16"] = bench_single(spin, torch, dev, sph, args.steps, args.warmup, flush, stream,
+                                                scheds=dict({k: spin.make_schedule(k) for k in
+                                                             ("STATIC", "SS", "GSS", "FAC")}, tuned=sph_tuned),
+                                                pairs=True)
+        extra["sphere-4096-W16"]["tuned"] = {
+            "kind": [k for k, v in spin.SCHED_NAMES.items() if v == sph_tuned.kind][0],
+            "min_chunk": sph_tuned.min_chunk, "num_workers": sph_tuned.num_workers, "group": sph_tuned.group,
+            "grid_div": sph_tuned.grid_div, "order": sph_tuned.order}
         extra["scene-1M-W64"] = bench_single(spin, torch, dev, wl.large_scene(), ex_steps, args.warmup, flush,
                                              stream, kinds=("STATIC", "SS", "GSS", "FAC"), pairs=True, e2e=True)
         # probabilistic factoring with sigma / mu of the group cost measured by
@@ -593,6 +601,21 @@ def bench_trace(spin, torch, dev, c, shape, stream, het=None):
         spin.si_mesh_destroy(mesh)
     return {"workload": c["name"], "by_schedule": res,
             "note": "imbalance = (latest - mean finishing time) / latest finishing time of the workers"}
+
+
+def _tuned_schedule(spin, torch, dev, c, stream, reps=5):
+    """The autotuner's choice for workload c (untimed; on its own mesh)."""
+    n, m, W = c["points"].shape[0], c["m"], c["W"]
+    tq = None if c["query_idx"] is None else torch.from_numpy(c["query_idx"]).to(dev)
+    mesh = spin.si_mesh_create(torch.from_numpy(c["points"]).to(dev), torch.from_numpy(c["normals"]).to(dev), n,
+                               stream)
+    out = torch.empty((m, W, W), dtype=torch.int32, device=dev)
+    try:
+        best, _ = spin.si_tune_mesh(mesh, tq, m, W, float(c["bin_size"]), float(c["cos_s"]), out, reps=reps,
+                                    stream=stream)
+    finally:
+        spin.si_mesh_destroy(mesh)
+    return best
 
 
 def _matching_inputs(spin, torch, dev, c, n_scene, stream):
