@@ -412,8 +412,16 @@ def run_ours(args):
             "kind": [k for k, v in spin.SCHED_NAMES.items() if v == sph_tuned.kind][0],
             "min_chunk": sph_tuned.min_chunk, "num_workers": sph_tuned.num_workers, "group": sph_tuned.group,
             "grid_div": sph_tuned.grid_div, "order": sph_tuned.order}
-        extra["scene-1M-W64"] = bench_single(spin, torch, dev, wl.large_scene(), ex_steps, args.warmup, flush,
-                                             stream, kinds=("STATIC", "SS", "GSS", "FAC"), pairs=True, e2e=True)
+        scn = wl.large_scene()
+        scn_tuned = _tuned_schedule(spin, torch, dev, scn, stream, reps=3)
+        extra["scene-1M-W64"] = bench_single(spin, torch, dev, scn, ex_steps, args.warmup, flush, stream,
+                                             scheds=dict({k: spin.make_schedule(k) for k in
+                                                          ("STATIC", "SS", "GSS", "FAC")}, tuned=scn_tuned),
+                                             pairs=True, e2e=True)
+        extra["scene-1M-W64"]["tuned"] = {
+            "kind": [k for k, v in spin.SCHED_NAMES.items() if v == scn_tuned.kind][0],
+            "min_chunk": scn_tuned.min_chunk, "num_workers": scn_tuned.num_workers, "group": scn_tuned.group,
+            "grid_div": scn_tuned.grid_div, "order": scn_tuned.order}
         # probabilistic factoring with sigma / mu of the group cost measured by
         # the probe run (a group's cost follows its candidate stream length)
         cov = _group_cost_cov(examined_per_image)
