@@ -271,15 +271,18 @@ def run_ours(args):
     # measured shared-atomic peak (denominator of the splat roofline)
     atom_peak = spin.si_peak_smem_atomics(0, stream)
     atom_spread = spin.si_peak_smem_atomics(1, stream)
-    # launch shape from the autotuner (untimed): group size and grid resolution
-    # are shared by every rule below; "tuned" is the tuner's full choice
+    # the autotuner's choice (untimed): rule, chunk, workers, group order and
+    # launch shape, timed below as "tuned"
     mesh = spin.si_mesh_create(tp, tn, n, stream)
     tuned, tuned_ms = spin.si_tune_mesh(mesh, None, m, W, B, cs, out, reps=3, stream=stream)
     spin.si_mesh_destroy(mesh)
-    shape = dict(group=tuned.group, grid_div=tuned.grid_div)
+    # the paper's rules (and the extra runs below) at the library's default
+    # shape, so that STATIC and the dynamic rules launch alike; "tuned" with
+    # the tuner's own shape
+    shape = {}
     configs = {name: spin.make_schedule(name, **shape) for name in SCHEDULES}
     configs["tuned"] = spin.make_schedule(tuned.kind, min_chunk=tuned.min_chunk, num_workers=tuned.num_workers,
-                                          order=tuned.order, **shape)
+                                          order=tuned.order, group=tuned.group, grid_div=tuned.grid_div)
     tuned_desc = {"kind": [k for k, v in spin.SCHED_NAMES.items() if v == tuned.kind][0],
                   "min_chunk": tuned.min_chunk, "num_workers": tuned.num_workers, "group": tuned.group,
                   "grid_div": tuned.grid_div,
@@ -385,7 +388,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": r["images_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config(c, {"schedule": best, "tuned": tuned_desc, "shape": shape,
+            "config": _config(c, {"schedule": best, "tuned": tuned_desc, "shape": shape or "library default",
                                   "parallelism": "replicas" if world > 1 else "single GPU"}),
             "culled_pairs_per_s": r["culled_pairs_per_s"], "culled_pairs_per_step": n_culled,
             "support_pairs_per_step": n_support, "examined_pairs_per_step": n_examined,
@@ -400,6 +403,12 @@ def run_ours(args):
             "gpu_launches": int(timed_launches), "clocks": clk}
     if not args.no_extra:
         from paper_1811_00901_gb300 import workloads as wl
+        import tempfile
+        # the tuning table as tuned on the bench workload; the sphere and scene
+        # tunings below add their own size classes, which the batched run
+        # (one rule per item from the nearest class) should not inherit
+        table = os.path.join(tempfile.mkdtemp(), "tuning.json")
+        spin.si_tune_save(table)
         ex_steps = args.steps
         extra = {}
         sph = wl.plain_sphere()
@@ -454,6 +463,8 @@ def run_ours(args):
             scheds={k: spin.make_schedule(k, binning="NEAREST") for k in ("STATIC", "FAC")})
         del out
         torch.cuda.empty_cache()
+        spin.si_tune_clear()
+        spin.si_tune_load(table)
         # one batched step writes 140 GB of images (about a second): 7 timed steps
         extra["batched-512-spheres"] = bench_batched(spin, torch, dev, min(ex_steps, 7), args.warmup, stream)
         torch.cuda.empty_cache()

@@ -95,15 +95,17 @@ si_status si_tune_mesh(si_mesh_t mesh, const int32_t *query_idx, int64_t m, int3
     int dev = 0;
     SI_CUDA(cudaGetDevice(&dev));
     const int auto_l2 = choose_log2_group(W, 0);
-    // stage 1: group size x grid resolution under GSS
+    // stage 1: group size x grid resolution under FAC (GSS's large first
+    // chunks make it the rule most sensitive to which groups come first, a
+    // poor guide for the grid the other rules will run on)
     std::vector<int> groups;
     for (int l = auto_l2; l >= 0 && l >= auto_l2 - 2; --l) groups.push_back(1 << l);
     const int divs[] = {4, 6, 8, 12};
-    si_schedule cur{SI_SCHED_GSS, 1, 0, 1 << auto_l2, 4};
+    si_schedule cur{SI_SCHED_FAC, 1, 0, 1 << auto_l2, 4};
     double cur_ms = 1e30;
     for (int g : groups)
         for (int d : divs) {
-            si_schedule s{SI_SCHED_GSS, 1, 0, g, d};
+            si_schedule s{SI_SCHED_FAC, 1, 0, g, d};
             double ms;
             si_status r = time_one(mesh, query_idx, m, W, bin_size, cos_support_angle, s, scratch_out, reps, st, &ms);
             if (r != SI_OK) return r;
