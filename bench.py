@@ -954,7 +954,8 @@ def run_profile_case(args):
 
 def run_profile_match(args):
     """A short run for profilers: `--profile-match` scene images of the
-    matching workload against the bench mesh's 100,000, `reps` BF16 calls."""
+    matching workload against the bench mesh's 100,000, `reps` calls in
+    `--profile-precision` (BF16 or FP32)."""
     import torch
 
     import paper_1811_00901_gb300 as spin
@@ -968,9 +969,10 @@ def run_profile_match(args):
     idx = torch.empty((args.profile_match, k), dtype=torch.int32, device=dev)
     val = torch.empty((args.profile_match, k), dtype=torch.float32, device=dev)
     for _ in range(args.reps):
-        spin.si_match(scene, args.profile_match, model, c["m"], c["W"], k, "BF16", idx, val, stream)
+        spin.si_match(scene, args.profile_match, model, c["m"], c["W"], k, args.profile_precision, idx, val, stream)
         torch.cuda.synchronize()
-    print(json.dumps({"profile_match": args.profile_match, "model_images": c["m"], "W": c["W"], "reps": args.reps}))
+    print(json.dumps({"profile_match": args.profile_match, "model_images": c["m"], "W": c["W"], "reps": args.reps,
+                      "precision": args.profile_precision}))
 
 
 def _small_workload(name):
@@ -992,7 +994,8 @@ def main():
                     help="run the workload `--reps` times under one schedule (for ncu)")
     ap.add_argument("--profile-workload", default="heightfield", choices=["heightfield", "sphere", "scene"])
     ap.add_argument("--profile-match", type=int, default=0, metavar="N_SCENE",
-                    help="run BF16 matching of N_SCENE images `--reps` times (for ncu)")
+                    help="run matching of N_SCENE images `--reps` times (for ncu)")
+    ap.add_argument("--profile-precision", default="BF16", choices=["BF16", "FP32"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=15)
