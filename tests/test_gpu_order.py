@@ -170,3 +170,40 @@ def test_cost_order_from_host_buffers():
                           spin.make_schedule("FAC", order=1), out)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(out.numpy(), ref)
+
+
+def test_tuner_rebuilds_grids_and_the_mesh_stays_usable():
+    """si_tune_mesh rebuilds the mesh's grids between its timed repetitions
+    (forgetting the batch graphs that held them); afterwards the mesh, a
+    batched call captured before the tuning and the tuner's choice all give
+    the grid-order STATIC images."""
+    import torch
+
+    import paper_1811_00901_gb300 as spin
+    pts, nrm = wl.heightfield(6000, 95)
+    W, B, c = 32, 0.01, wl.cos_deg(60.0)
+    ref, _ = gpu_run(pts, nrm, W, B, c, schedule=spin.make_schedule("STATIC"))
+    dev = torch.device("cuda:0")
+    mesh = spin.si_mesh_create(torch.from_numpy(pts).to(dev), torch.from_numpy(nrm).to(dev))
+    try:
+        out = torch.empty((6000, W, W), dtype=torch.int32, device=dev)
+        item = [dict(mesh=mesh, query_idx=None, m=6000, W=W, bin_size=B, cos_s=c, out=out)]
+        spin.si_generate_batched(item, spin.make_schedule("FAC"))  # a cached graph holding the grid
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy(), ref)
+        spin.si_tune_clear()
+        best, ms = spin.si_tune_mesh(mesh, None, 6000, W, B, c, out, reps=2)
+        assert ms > 0 and best.kind in (0, 1, 2, 3) and best.order in (0, 1)
+        for sched in (best, spin.make_schedule("FAC", order=1)):
+            out.fill_(-1)
+            spin.si_generate(mesh, None, 6000, W, B, c, sched, out)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(out.cpu().numpy(), ref)
+        out.fill_(-1)
+        spin.si_generate_batched(item, spin.make_schedule("FAC"))
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy(), ref)
+        spin.si_get_stats(mesh)
+    finally:
+        spin.si_tune_clear()
+        spin.si_mesh_destroy(mesh)
